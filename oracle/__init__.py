@@ -1,0 +1,142 @@
+"""CPU oracle of the BSP sample sort (Gerbessiotis & Siniolakis, Fig. 1 and Fig. 3).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()`` and
+by the cpu_baseline / reference legs of ``bench.py``.  The product path (the
+package ``paper_1408_6729_gb300``) never imports it.
+
+The arithmetic lives in ``bsp_oracle.c`` (plain C, compiled here with gcc on
+first use); this module only marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bsp_oracle.c")
+_LIB = os.path.join(_HERE, "libbsp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+U32, I32, F32, F64 = 0, 1, 2, 3
+REGULAR, RANDOM = 0, 1
+
+DTYPE_CODE = {np.dtype(np.uint32): U32, np.dtype(np.int32): I32,
+              np.dtype(np.float32): F32, np.dtype(np.float64): F64}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("runs", ctypes.c_int32), ("s", ctypes.c_int64),
+                ("sampling", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in
+                ("n", "p", "R", "s", "m", "M", "x", "q", "sample_size")] + \
+               [("sampling", ctypes.c_int32)]
+
+
+RECORD_DTYPE = np.dtype([("phi", np.uint64), ("tag", np.uint64),
+                         ("pad", np.uint32), ("reserved", np.uint32)])
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99 + __int128)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
+                                   "-o", tmp, _SRC])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.oracle_sort.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, ctypes.POINTER(Params),
+                                    P, P, P, P, P, P, P]
+        lib.oracle_sort.restype = ctypes.c_int
+        lib.oracle_plan_of.argtypes = [ctypes.c_int64, ctypes.POINTER(Params), ctypes.POINTER(Plan)]
+        lib.oracle_plan_of.restype = ctypes.c_int
+        lib.oracle_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_draw.restype = ctypes.c_uint64
+        lib.oracle_position.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64]
+        lib.oracle_position.restype = ctypes.c_int64
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def make_params(p, s=0, runs=0, sampling=REGULAR, seed=0) -> Params:
+    return Params(p=int(p), runs=int(runs), s=int(s), sampling=int(sampling), reserved=0,
+                  seed=int(seed) & (2**64 - 1))
+
+
+def plan(n, p, s=0, runs=0, sampling=REGULAR, seed=0) -> Plan | None:
+    """Resolved parameters (defaults of Sec. 6.1); None when they are invalid."""
+    pl = Plan()
+    prm = make_params(p, s, runs, sampling, seed)
+    rc = _load().oracle_plan_of(int(n), ctypes.byref(prm), ctypes.byref(pl))
+    return None if rc else pl
+
+
+def draw(seed: int, j: int) -> int:
+    """Draw j of the random-sample stream: Philox4x64-10, key (seed,0), counter (j//4,0,0,0)."""
+    return int(_load().oracle_draw(seed & (2**64 - 1), j))
+
+
+def position(seed: int, j: int, n: int) -> int:
+    return int(_load().oracle_position(seed & (2**64 - 1), j, n))
+
+
+@dataclass
+class Result:
+    keys: np.ndarray
+    vals: np.ndarray | None
+    bucket_sizes: np.ndarray
+    pad_sizes: np.ndarray
+    sample: np.ndarray | None
+    splitters: np.ndarray
+    bucket_of: np.ndarray | None
+    plan: Plan
+
+
+def sort(keys: np.ndarray, p: int, s: int = 0, runs: int = 0, sampling: int = REGULAR,
+         seed: int = 0, vals: np.ndarray | None = None, want_sample: bool = True,
+         want_bucket_of: bool = False) -> Result:
+    """Run the BSP simulation; raises ValueError on invalid parameters."""
+    keys = np.ascontiguousarray(keys)
+    code = DTYPE_CODE[keys.dtype]
+    n = keys.shape[0]
+    pl = plan(n, p, s, runs, sampling, seed)
+    if pl is None:
+        raise ValueError("invalid parameters")
+    if vals is not None:
+        vals = np.ascontiguousarray(vals, dtype=np.uint32)
+        assert vals.shape[0] == n
+    keys_out = np.empty_like(keys)
+    vals_out = np.empty(n, np.uint32) if vals is not None else None
+    sizes = np.zeros(pl.p, np.int64)
+    pads = np.zeros(pl.p, np.int64)
+    sample = np.zeros(pl.sample_size, RECORD_DTYPE) if (want_sample and n > 0) else None
+    spl = np.zeros(max(pl.p - 1, 0), RECORD_DTYPE)
+    bof = np.full(n, -1, np.int32) if want_bucket_of else None
+    prm = make_params(p, s, runs, sampling, seed)
+    rc = _load().oracle_sort(code, _ptr(keys), _ptr(vals), n, ctypes.byref(prm), _ptr(keys_out),
+                             _ptr(vals_out), _ptr(sizes), _ptr(pads), _ptr(sample), _ptr(spl),
+                             _ptr(bof))
+    if rc:
+        raise ValueError(f"oracle_sort failed with status {rc}")
+    return Result(keys_out, vals_out, sizes, pads, sample, spl, bof, pl)
