@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 BSP sample sort (one JSON line on stdout, rank 0).
+
+Step = one whole sort (sampling, sample sort, splitter selection, routing,
+bucket sort) of the workload below, inputs resident in HBM.  Under torchrun
+every rank sorts its own independent instance (the sort shards into
+independent problems; no collective is on the data path): weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the paper's algorithm as an explicit
+BSP simulation, single-threaded) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import bsp_inputs as gen  # noqa: E402
+
+# The workload the metric is quoted on: 2^28 int32 keys of the paper's uniform
+# input [U], p = 4096 buckets, random oversampling with the paper's default
+# s = 2 lg^2 n = 1568 (sample 6,422,527 keys), keys only.
+WORKLOADS = {
+    "uniform_2e28_int32_p4096_random": dict(n=1 << 28, p=4096, sampling=1, s=0, runs=0, pairs=False,
+                                           make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    "uniform_2e28_int32_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=False,
+                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    "zipf_2e28_int32_pairs_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=True,
+                                               make=lambda n, p, seed: gen.zipf(n, seed=seed)),
+}
+DEFAULT_WORKLOAD = "uniform_2e28_int32_p4096_random"
+METRIC = "keys/sec and % HBM roofline, 2^28 int32; learned/batched vs plain, bit-exact"
+
+# Algorithmic bytes per key of each timed phase (keys only, 4-byte keys): the
+# routing pass reads every key and writes it once (8 B); the bucket sort reads
+# and writes every key once (8 B).  With 4-byte payloads both double.
+PHASES = ["sample", "sample_sort", "splitters", "route", "bucket_sort"]
+PHASE_KERNEL = {"route": "route_kernel", "bucket_sort": "bucket_sort_kernel"}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
+# ncu capture (profiles/*.md), valid while the kernel source is unchanged.
+NCU_TRAFFIC = {}  # kernel -> (bytes per key, sha256 of the source file at capture)
+KERNEL_SOURCE = {"route_kernel": "paper_1408_6729_gb300/csrc/route.cu",
+                 "bucket_sort_kernel": "paper_1408_6729_gb300/csrc/bucket.cu"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_hash(path):
+    return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def oracle_rate(wl, budget_s=12.0, seed=1):
+    """Oracle keys/s on a bounded sample of the workload: same generator, p, s,
+    runs and mode; n doubles from 2^20 until one sort takes budget_s/4."""
+    import oracle
+    oracle.build()
+    n = 1 << 20
+    while True:
+        keys = wl["make"](n, wl["p"], seed)
+        vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
+        t0 = time.perf_counter()
+        oracle.sort(keys, wl["p"], wl["s"], wl["runs"], wl["sampling"], seed=seed, vals=vals, want_sample=False)
+        t = time.perf_counter() - t0
+        if t > budget_s / 4 or n >= wl["n"]:
+            return n / t, n, wl["s"], wl["runs"], t
+        n *= 2
+
+
+def run_reference(args, wl, name):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    rate, n, s, runs, t = oracle_rate(wl, budget_s=min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    times = []
+    import oracle
+    keys = wl["make"](n, wl["p"], 1)
+    vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.sort(keys, wl["p"], s, runs, wl["sampling"], seed=1, vals=vals, want_sample=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = n * len(times) / tot
+    sample = f"{n} keys of the workload's generator, p={wl['p']}, s={s}, runs={runs or wl['p']}, one oracle sort per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": name, "n": wl["n"], "p": wl["p"]},
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, wl, name):
+    import torch
+    import paper_1408_6729_gb300 as bsps
+    from paper_1408_6729_gb300 import build as lib_build
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        lib_build.build()
+    barrier(pg)
+    lib_build.build()  # no-op once built
+    n, p = wl["n"], wl["p"]
+    code = bsps.BSPS_I32
+    prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank)
+    plan = bsps.bsps_get_plan(n, code, prm, wl["pairs"])
+    keys_h = wl["make"](n, p, 1 + rank)
+    kin = torch.from_numpy(keys_h).to(dev)
+    kout = torch.empty_like(kin)
+    vin = vout = None
+    if wl["pairs"]:
+        vin = torch.arange(n, dtype=torch.int32, device=dev)
+        vout = torch.empty_like(vin)
+    sizes = torch.empty(p, dtype=torch.int64, device=dev)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    # one set of phase events per timed step, created (recorded once) up front
+    step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(bsps.BSPS_PHASES)]
+                   for _ in range(args.steps)]
+    for evs in step_events:
+        for e in evs:
+            e.record(stream)
+    torch.cuda.synchronize()
+    launches = ctypes.c_int32(0)
+
+    def step(timed_events=None, count=None):
+        rc = bsps.bsps_sort_debug(kin, vin, kout, vout, n, code, prm, sizes, ws, phase_events=timed_events,
+                                  launches=count)
+        if rc:
+            raise RuntimeError(bsps.bsps_strerror(rc))
+
+    for _ in range(args.warmup):
+        step()
+    st = bsps.bsps_read_stats(ws)
+    if st.status:
+        raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
+
+    # timed region: K whole sorts, back to back on one stream
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_launches = 0
+    with ClockSampler(local) as clk:
+        barrier(pg)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for k in range(args.steps):
+            step(step_events[k], launches)
+            total_launches += launches.value
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    elapsed_ms = start.elapsed_time(end)
+    phase_ms = {k: sum(evs[i].elapsed_time(evs[i + 1]) for evs in step_events) for i, k in enumerate(PHASES)}
+    elapsed_ms = max_over_ranks(pg, elapsed_ms)
+    st = bsps.bsps_read_stats(ws)
+    if st.status:
+        raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
+    # sanity of the last output (not part of the timed region)
+    ok = bool((kout[1:] >= kout[:-1]).all().item()) and int(kout.to(torch.int64).sum().item()) == int(
+        kin.to(torch.int64).sum().item())
+    if not ok:
+        raise RuntimeError("output is not a sorted permutation of the input")
+
+    # end to end through the C ABI with host buffers: H2D of the keys, the sort,
+    # D2H of the sorted keys, every step
+    h_in = torch.from_numpy(keys_h).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(1):
+        kin.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(kout, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        kin.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(kout, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1))
+    assert np.array_equal(h_out.numpy()[:: max(1, n // 4096)], kout.cpu().numpy()[:: max(1, n // 4096)])
+
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    kb = 4 + (4 if wl["pairs"] else 0)
+    per_step = {k: v / args.steps for k, v in phase_ms.items()}
+    dom = max(("route", "bucket_sort"), key=lambda k: per_step[k])
+    kern = PHASE_KERNEL[dom]
+    alg_bytes = n * 2 * kb
+    achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
+    traffic = None
+    if kern in NCU_TRAFFIC and NCU_TRAFFIC[kern][1] == source_hash(KERNEL_SOURCE[kern]):
+        traffic = NCU_TRAFFIC[kern][0] * n
+    ms_step = elapsed_ms / args.steps
+    value = world * n / (ms_step * 1e-3)
+    b_alg = 4 * kb + plan.sample_size * (4 + 8) / n + (kb if wl["sampling"] == 0 else 0)
+    cpu = None
+    if world == 1:
+        rate, ns, s_used, runs_used, t_used = oracle_rate(wl)
+        cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ns} keys of the same generator, p={p}, s={s_used}, "
+                         f"runs={runs_used or p}, {t_used:.1f} s single-threaded"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": name, "n": n, "p": p, "sampling": "random" if wl["sampling"] else "regular",
+                   "s": plan.s, "runs": plan.R, "sample_size": plan.sample_size, "pairs": wl["pairs"],
+                   "refine": plan.refine, "bucket_cluster": plan.bucket_cluster,
+                   "l2": "inputs (1 GiB) larger than L2 (126 MB); no flush",
+                   "parallelism": f"independent sorts x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic, "kernel": kern,
+                     "peak_source": f"{pk_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes},
+        "path_roofline": {"alg_bytes_per_key": b_alg,
+                          "frac": n * b_alg / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"]},
+        "phases_ms": per_step,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "keys/s",
+                "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+        "gpu_launches": total_launches,
+        "clocks": clk.summary(),
+        "stats": {"max_bucket": st.max_bucket, "max_vbucket": st.max_vbucket, "slow_buckets": st.slow_buckets,
+                  "imbalance": st.max_bucket / (n / p) - 1},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, args.workload)
+    else:
+        run_gpu(args, wl, args.workload)
+
+
+if __name__ == "__main__":
+    main()

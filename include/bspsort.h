@@ -1,0 +1,201 @@
+/*
+ * bspsort.h -- C ABI of the GB300 (sm_103a) BSP sample sort.
+ *
+ * The library implements the data-parallel path of the BSP sample sorts of
+ * Gerbessiotis & Siniolakis, "BSP Sorting: An experimental Study":
+ *   Sort_Det_BSP  (Fig. 1, Sec. 5.1)  -- regular (deterministic) oversampling
+ *   Sort_IRan_BSP (Fig. 3, Sec. 5.2)  -- random oversampling
+ * with the duplicate-key handling of Sec. 5.1.1.  On one GPU the p BSP
+ * processors become p buckets: every key is classified against the p-1
+ * splitters (Fig. 2 step 9), routed once through HBM in input order
+ * (Fig. 1 step 11), and each bucket is sorted in on-chip memory (Fig. 2 step 12).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *    never allocates, frees or retains them.  h_* pointers are host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is asynchronous and stream-ordered; only bsps_read_stats()
+ *    synchronises (the stream it is given).
+ *  - Key order: a key's bit pattern is mapped to an unsigned integer phi
+ *    (uint32: identity; int32: flip the sign bit; float32/float64: IEEE 754
+ *    totalOrder, i.e. -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN) and
+ *    ties are broken by input position (Sec. 5.1.1: processor id, then local
+ *    index).  The output is the stable sort in that order.
+ *  - Return value: BSPS_OK (0) or a negative BSPS_ERR_* code.  Argument
+ *    errors are detected on the host before anything is launched.  Errors
+ *    found on the device (bucket overflow, a bounded wait that expired) are
+ *    recorded in the workspace and returned by bsps_read_stats().
+ *  - In-place use (input == output) is rejected.  Inputs are never modified.
+ */
+#ifndef BSPSORT_H
+#define BSPSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* key types */
+typedef enum { BSPS_U32 = 0, BSPS_I32 = 1, BSPS_F32 = 2, BSPS_F64 = 3 } bsps_dtype;
+
+/* oversampling: Sort_Det_BSP (Fig. 1) or Sort_IRan_BSP (Fig. 3) */
+typedef enum { BSPS_REGULAR = 0, BSPS_RANDOM = 1 } bsps_sampling;
+
+/* classification of keys against the splitters (Fig. 2 step 9) */
+typedef enum { BSPS_TREE = 0, BSPS_LEARNED = 1 } bsps_classify;
+
+#define BSPS_OK 0
+#define BSPS_ERR_INVALID_ARG (-1)
+#define BSPS_ERR_WORKSPACE_TOO_SMALL (-2)
+#define BSPS_ERR_UNSUPPORTED_DTYPE (-3)
+#define BSPS_ERR_BUCKET_OVERFLOW (-4)
+#define BSPS_ERR_CUDA (-5)
+#define BSPS_ERR_DEVICE_TIMEOUT (-6)
+#define BSPS_ERR_TOO_LARGE (-7)
+
+/*
+ * Parameters, as the paper states them.
+ *   p         number of buckets (the paper's processors), >= 1.
+ *   runs      R, the number of virtual processors holding contiguous blocks of
+ *             ceil(n/R) keys (regular mode); 0 -> R = p, as in the paper.
+ *   s         oversampling factor.  Regular mode: samples per block (Fig. 1
+ *             step 4, s = r*p); 0 -> r = ceil(lg lg n) (Sec. 6.1).  Random
+ *             mode: the sample has s*p - 1 keys (Fig. 3 step 4); 0 -> s = 2 *
+ *             ceil(lg n)^2 (Sec. 6.1, omega_n^2 = lg n).
+ *   sampling  bsps_sampling.
+ *   classify  bsps_classify.
+ *   seed      random-mode sample stream: draw j is word (j mod 4) of
+ *             Philox4x64-10 with key (seed, 0) and counter (floor(j/4),0,0,0);
+ *             the sampled position is floor(draw * n / 2^64).
+ *   refine    internal sub-bucket factor (power of two; 0 -> automatic).  It
+ *             changes neither the splitters nor any result, only how finely
+ *             buckets are cut before the on-chip sort.
+ *   capacity_pct  random mode: capacity of each bucket region in percent of
+ *             the mean sub-bucket size (0 -> automatic).  Regular mode ignores
+ *             it and uses the exact bound of Lemma 5.1.
+ */
+typedef struct {
+    int32_t p;
+    int32_t runs;
+    int64_t s;
+    int32_t sampling;
+    int32_t classify;
+    uint64_t seed;
+    int32_t refine;
+    int32_t capacity_pct;
+} bsps_params;
+
+/* A sample or splitter record of the total order: (pad, phi, tag), tag =
+ * k*M + j for the key at local index j of virtual processor k (Sec. 5.1.1);
+ * pads (Lemma 5.1's padding) have phi = 2^64-1 and pad = 1. */
+typedef struct {
+    uint64_t phi;
+    uint64_t tag;
+    uint32_t pad;
+    uint32_t reserved;
+} bsps_record;
+
+/* Resolved parameters of one call (filled by bsps_get_plan). */
+typedef struct {
+    int64_t n, p, R, s, m, M, x, q, sample_size;
+    int32_t sampling, dtype;
+    int64_t refine;          /* sub-buckets per bucket */
+    int64_t vbuckets;        /* p * refine */
+    int64_t capacity;        /* keys per sub-bucket region */
+    int32_t run_cluster;     /* CTAs per block sort (regular mode) */
+    int32_t bucket_cluster;  /* CTAs per sub-bucket sort */
+    int64_t route_tiles;
+    size_t workspace_bytes;
+} bsps_plan;
+
+/* Device-side statistics and errors of the last call on a workspace. */
+typedef struct {
+    int32_t status;          /* BSPS_OK or the first device-side error */
+    int32_t overflow;        /* nonzero if a bucket exceeded its region */
+    int32_t timeouts;        /* bounded waits that expired */
+    int32_t slow_buckets;    /* sub-buckets sorted by the out-of-core path */
+    int64_t max_bucket;      /* largest bucket, real keys only */
+    int64_t max_vbucket;     /* largest sub-bucket */
+    int64_t mispredicted;    /* learned classifier: keys whose prediction was corrected */
+    int64_t correction_steps;/* learned classifier: total search steps of the corrections */
+} bsps_stats;
+
+/* Optional diagnostics; every field may be NULL / 0.
+ *   sample, splitters, bucket_of, pad_sizes: DEVICE buffers the call fills.
+ *   phase_events: BSPS_PHASES cudaEvent_t handles (created by the caller) that
+ *     the call records on its stream at the phase boundaries: before sampling,
+ *     after sampling, after the sample sort, after splitter selection, after
+ *     routing, after the bucket sort.
+ *   launches: HOST int32 that receives the number of kernels the call launched. */
+#define BSPS_PHASES 6
+typedef struct {
+    bsps_record *sample;     /* plan.sample_size records, sorted */
+    bsps_record *splitters;  /* p-1 records */
+    int32_t *bucket_of;      /* n bucket ids, by input position */
+    int64_t *pad_sizes;      /* p pad counts (regular mode) */
+    void *const *phase_events;
+    int32_t *launches;
+} bsps_debug;
+
+/*
+ * bsps_get_plan -- resolve the paper's defaults and the internal layout.
+ * with_payload: 1 if 32-bit payloads travel with the keys.
+ * Returns BSPS_ERR_INVALID_ARG when p < 1, n < 0, s < 0, regular mode has
+ * R*s not a multiple of p (the splitter stride q = R*s/p of Fig. 1 step 6
+ * must be an integer), or refine is not a power of two; BSPS_ERR_TOO_LARGE
+ * when n >= 2^30 or the padded key count exceeds 32-bit tags.
+ */
+int bsps_get_plan(int64_t n, int32_t dtype, const bsps_params *prm, int32_t with_payload,
+              bsps_plan *out);
+
+/* bsps_workspace_size -- bytes of device workspace the sort calls need. */
+int bsps_workspace_size(int64_t n, int32_t dtype, const bsps_params *prm, int32_t with_payload,
+                        size_t *bytes);
+
+/*
+ * bsps_sort_keys -- sort n keys (Fig. 1 / Fig. 3 with per-key classification).
+ *   d_keys_in      n keys (4 or 8 bytes each, per dtype)
+ *   d_keys_out     n keys, sorted; must not alias d_keys_in
+ *   d_bucket_sizes p int64 counts of keys per bucket (nullable)
+ *   d_ws, ws_bytes workspace of at least bsps_workspace_size() bytes,
+ *                  aligned to 256 bytes; reused freely between calls that are
+ *                  ordered on the same stream
+ */
+int bsps_sort_keys(const void *d_keys_in, void *d_keys_out, int64_t n, int32_t dtype,
+                   const bsps_params *prm, int64_t *d_bucket_sizes, void *d_ws, size_t ws_bytes,
+                   void *stream);
+
+/*
+ * bsps_sort_pairs -- as bsps_sort_keys, with a 32-bit payload per key.  The
+ * sort is stable: payloads of equal keys keep their input order (Sec. 5.1.1).
+ */
+int bsps_sort_pairs(const void *d_keys_in, const uint32_t *d_vals_in, void *d_keys_out,
+                    uint32_t *d_vals_out, int64_t n, int32_t dtype, const bsps_params *prm,
+                    int64_t *d_bucket_sizes, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * bsps_sort_debug -- bsps_sort_pairs (d_vals_in may be NULL for keys only)
+ * that also writes the optional diagnostics of `dbg`.
+ */
+int bsps_sort_debug(const void *d_keys_in, const uint32_t *d_vals_in, void *d_keys_out,
+                    uint32_t *d_vals_out, int64_t n, int32_t dtype, const bsps_params *prm,
+                    int64_t *d_bucket_sizes, const bsps_debug *dbg, void *d_ws, size_t ws_bytes,
+                    void *stream);
+
+/*
+ * bsps_read_stats -- synchronise `stream` and read the statistics and the
+ * device-side status of the last sort that used workspace d_ws.
+ * Returns stats->status.
+ */
+int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream);
+
+/* bsps_strerror -- static text for a status code. */
+const char *bsps_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSPSORT_H */

@@ -1,0 +1,325 @@
+// api.cu -- the C ABI: parameter resolution (the paper's defaults), the
+// workspace layout, and the order of the steps on the stream.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace bsps {
+
+static int64_t ceil_log2(int64_t n) {
+    int64_t r = 0;
+    while (((int64_t)1 << r) < n) ++r;
+    return r;
+}
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+static int items_for(int key_bytes, bool slot) {
+    if (slot) return key_bytes == 8 ? kPairItems64 : kPairItems32;
+    return key_bytes == 8 ? kBucketItems64 : kBucketItems32;
+}
+
+// Resolve the parameters and the internal layout.  Defaults follow Sec. 6.1:
+// regular oversampling uses s = r*p with r = ceil(lg lg n) (omega_n = lg lg n,
+// Fig. 1 step 1); random oversampling uses s = 2 lg^2 n (omega_n^2 = lg n,
+// Fig. 3 step 1), with lg n rounded up.
+static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Plan &pl) {
+    if (!prm) return BSPS_ERR_INVALID_ARG;
+    if (dtype < BSPS_U32 || dtype > BSPS_F64) return BSPS_ERR_UNSUPPORTED_DTYPE;
+    if (n < 0 || prm->p < 1 || prm->s < 0 || prm->runs < 0 || prm->refine < 0 || prm->capacity_pct < 0)
+        return BSPS_ERR_INVALID_ARG;
+    if (prm->sampling != BSPS_REGULAR && prm->sampling != BSPS_RANDOM) return BSPS_ERR_INVALID_ARG;
+    if (prm->classify != BSPS_TREE && prm->classify != BSPS_LEARNED) return BSPS_ERR_INVALID_ARG;
+    if (prm->refine != 0 && !is_pow2(prm->refine)) return BSPS_ERR_INVALID_ARG;
+    if (n >= ((int64_t)1 << 30)) return BSPS_ERR_TOO_LARGE;
+    std::memset(&pl, 0, sizeof(pl));
+    pl.n = n;
+    pl.p = prm->p;
+    pl.R = prm->runs > 0 ? prm->runs : prm->p;
+    pl.sampling = prm->sampling;
+    pl.classify = prm->classify;
+    pl.dtype = dtype;
+    pl.pairs = pairs;
+    pl.seed = prm->seed;
+    pl.key_bytes = dtype == BSPS_F64 ? 8 : 4;
+    if (prm->s > ((int64_t)1 << 31) || prm->runs > ((int64_t)1 << 30)) return BSPS_ERR_TOO_LARGE;
+    const int64_t clg = n >= 2 ? ceil_log2(n) : 1;
+    pl.m = (n + pl.R - 1) / pl.R;
+    if (pl.sampling == BSPS_REGULAR) {
+        int64_t r = 1;
+        while (((int64_t)1 << r) < clg) ++r;
+        pl.s = prm->s > 0 ? prm->s : r * pl.p;
+        pl.M = pl.s * ((pl.m + pl.s - 1) / pl.s);
+        if (pl.M == 0) pl.M = pl.s;
+        pl.x = pl.M / pl.s;
+        if ((pl.R * pl.s) % pl.p != 0 || pl.R * pl.s < pl.p) return BSPS_ERR_INVALID_ARG;
+        pl.q = pl.R * pl.s / pl.p;
+        pl.Q = pl.q;
+        pl.sample_size = pl.R * pl.s;
+        if (n + pl.R * pl.M >= ((int64_t)1 << 32)) return BSPS_ERR_TOO_LARGE;  // 32-bit pad tags
+    } else {
+        pl.s = prm->s > 0 ? prm->s : 2 * clg * clg;
+        pl.M = pl.m;
+        pl.x = 0;
+        pl.q = pl.s;
+        pl.Q = pl.s;
+        pl.sample_size = pl.s * pl.p - 1;
+    }
+    if (pl.sample_size >= ((int64_t)1 << 31) || pl.p > ((int64_t)1 << 24)) return BSPS_ERR_TOO_LARGE;
+
+    // sub-buckets: the smallest refinement whose expected size fits one
+    // cluster's shared memory with head room for the sampling imbalance
+    const int64_t cap_cta = (int64_t)kSortThreads * items_for(pl.key_bytes, pairs);
+    auto headroom = [&](int64_t B) {
+        return pl.sampling == BSPS_RANDOM ? 1.0 + 5.0 / std::sqrt((double)std::max<int64_t>(1, pl.Q / B))
+                                          : 1.25;
+    };
+    int64_t B = prm->refine;
+    if (B == 0) {
+        B = 1;
+        while (B * 2 <= pl.Q && (double)n / (pl.p * B) * headroom(B) > 8.0 * cap_cta) B *= 2;
+    }
+    if (B > pl.Q) return BSPS_ERR_INVALID_ARG;
+    pl.B = B;
+    pl.P = pl.p * B;
+    const double expect = (double)n / pl.P * headroom(B);
+    pl.bucket_cl = 8;
+    for (int cl = 1; cl <= 8; cl *= 2)
+        if (expect <= (double)cl * cap_cta) { pl.bucket_cl = cl; break; }
+
+    if (pl.sampling == BSPS_REGULAR) {
+        // Lemma 5.1, refined: a sub-bucket spans at most ceil(Q/B) sample
+        // records, hence at most ceil(Q/B)*x + (R-1)*(x-1) + 1 records.
+        const int64_t qb = (pl.Q + B - 1) / B;
+        pl.cap = std::min<int64_t>(std::max<int64_t>(n, 1), qb * pl.x + (pl.R - 1) * (pl.x > 0 ? pl.x - 1 : 0) + 1);
+        const int64_t cap_run = (int64_t)kSortThreads * (pl.key_bytes == 8 ? kRunItems64 : kRunItems32);
+        pl.run_cl = 0;
+        for (int cl = 1; cl <= 8; cl *= 2)
+            if (pl.m <= cl * cap_run) { pl.run_cl = cl; break; }
+        if (pl.run_cl == 0) return BSPS_ERR_TOO_LARGE;
+    } else {
+        const double pct = prm->capacity_pct > 0
+                               ? prm->capacity_pct / 100.0
+                               : 1.0 + 8.0 / std::sqrt((double)std::max<int64_t>(1, pl.Q / B));
+        pl.cap = std::min<int64_t>(std::max<int64_t>(n, 1), (int64_t)std::ceil((double)n / pl.P * pct) + 64);
+        pl.run_cl = 1;
+    }
+    if ((double)pl.P * pl.cap >= 4.0e9) return BSPS_ERR_TOO_LARGE;
+    pl.tiles = (n + kRouteTile - 1) / kRouteTile;
+    pl.lsd_tiles = (pl.sample_size + kLsdTile - 1) / kLsdTile;
+    pl.lsd_npos = 4 + pl.key_bytes;
+    if (route_smem_bytes(pl) > 227 * 1024) return BSPS_ERR_TOO_LARGE;
+
+    // workspace size
+    int64_t o = 0;
+    auto take = [&](int64_t bytes) { int64_t at = o; o = align_up(o + std::max<int64_t>(bytes, 1), 256); return at; };
+    take(sizeof(DevStatus));
+    const int64_t S = std::max<int64_t>(pl.sample_size, 1);
+    take(S * pl.key_bytes); take(S * pl.key_bytes);
+    take(S * 4); take(S * 4);
+    take(std::max<int64_t>(pl.lsd_tiles, 1) * 256 * 4);
+    take(16 * 256 * 4);
+    take(64 * 4);
+    take(pl.P * pl.key_bytes);
+    take(pl.P * 4);
+    take((kLutCells + 2) * 4);
+    take(64);
+    take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
+    take(pl.P * pl.cap * pl.key_bytes);
+    take(pairs ? pl.P * pl.cap * 4 : 0);
+    take(pl.P * 4);
+    take((pl.P + 1) * 8);
+    take(pl.P * 4);
+    pl.ws_bytes = (size_t)o;
+    return BSPS_OK;
+}
+
+static Layout make_layout(const Plan &pl, void *ws) {
+    unsigned char *b = (unsigned char *)ws;
+    int64_t o = 0;
+    auto take = [&](int64_t bytes) { int64_t at = o; o = align_up(o + std::max<int64_t>(bytes, 1), 256); return (void *)(b + at); };
+    Layout l;
+    const int64_t S = std::max<int64_t>(pl.sample_size, 1);
+    l.status = (DevStatus *)take(sizeof(DevStatus));
+    l.sphi[0] = take(S * pl.key_bytes);
+    l.sphi[1] = take(S * pl.key_bytes);
+    l.stag[0] = (uint32_t *)take(S * 4);
+    l.stag[1] = (uint32_t *)take(S * 4);
+    l.lsd_counts = (uint32_t *)take(std::max<int64_t>(pl.lsd_tiles, 1) * 256 * 4);
+    l.lsd_hist = (uint32_t *)take(16 * 256 * 4);
+    l.lsd_table = (int32_t *)take(64 * 4);
+    l.vphi = take(pl.P * pl.key_bytes);
+    l.vtag = (uint32_t *)take(pl.P * 4);
+    l.lut = (uint32_t *)take((kLutCells + 2) * 4);
+    l.lutp = take(64);
+    l.state = (uint32_t *)take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
+    l.reg_keys = take(pl.P * pl.cap * pl.key_bytes);
+    l.reg_vals = (uint32_t *)take(pl.pairs ? pl.P * pl.cap * 4 : 0);
+    l.vsize = (uint32_t *)take(pl.P * 4);
+    l.voff = (uint64_t *)take((pl.P + 1) * 8);
+    l.slow_list = (uint32_t *)take(pl.P * 4);
+    return l;
+}
+
+static void to_public(const Plan &p, bsps_plan *out) {
+    out->n = p.n; out->p = p.p; out->R = p.R; out->s = p.s; out->m = p.m; out->M = p.M; out->x = p.x;
+    out->q = p.q; out->sample_size = p.sample_size; out->sampling = p.sampling; out->dtype = p.dtype;
+    out->refine = p.B; out->vbuckets = p.P; out->capacity = p.cap; out->run_cluster = p.run_cl;
+    out->bucket_cluster = p.bucket_cl; out->route_tiles = p.tiles; out->workspace_bytes = p.ws_bytes;
+}
+
+// Kernels one call launches (the sample sort launches all its pass slots;
+// slots whose byte position is constant return at once).
+static int kernels_per_call(const Plan &pl) {
+    int k = 1;                                   // sample (random draw or block sort)
+    if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
+    k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
+    k += 2;                                      // splitters, radix index
+    k += 2;                                      // routing, bucket offsets
+    k += 2;                                      // cluster bucket sort, out-of-core bucket sort
+    return k;
+}
+
+static int debug_kernels(const Ctx &c) {
+    const Plan &p = c.pl;
+    int k = 0;
+    if (c.dbg.sample && p.sample_size > 0) ++k;
+    if (c.dbg.splitters && p.p > 1) ++k;
+    if (c.dbg.bucket_of && p.n > 0) ++k;
+    if (c.dbg.pad_sizes && p.sampling == BSPS_REGULAR && p.R * p.M > p.n) ++k;
+    return k;
+}
+
+#define BSPS_CUDA(call)                                   \
+    do {                                                  \
+        if ((call) != cudaSuccess) return BSPS_ERR_CUDA;  \
+    } while (0)
+
+static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uint32_t *vals_out, int64_t n,
+               int32_t dtype, const bsps_params *prm, int64_t *bucket_sizes, const bsps_debug *dbg, void *ws,
+               size_t ws_bytes, void *stream) {
+    Ctx c;
+    std::memset(&c, 0, sizeof(c));
+    const int pairs = vals_in != nullptr;
+    int rc = make_plan(n, dtype, prm, pairs, c.pl);
+    if (rc) return rc;
+    if (c.pl.classify == BSPS_LEARNED) return BSPS_ERR_INVALID_ARG;  // see bsps_sort_learned
+    if (pairs && !vals_out) return BSPS_ERR_INVALID_ARG;
+    if (n > 0 && (!keys_in || !keys_out)) return BSPS_ERR_INVALID_ARG;
+    if (n > 0 && keys_in == keys_out) return BSPS_ERR_INVALID_ARG;
+    if (pairs && (const void *)vals_in == (const void *)vals_out) return BSPS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < c.pl.ws_bytes) return BSPS_ERR_WORKSPACE_TOO_SMALL;
+    if (((uintptr_t)ws & 255) != 0) return BSPS_ERR_INVALID_ARG;
+    c.ly = make_layout(c.pl, ws);
+    c.keys_in = keys_in;
+    c.vals_in = vals_in;
+    c.keys_out = keys_out;
+    c.vals_out = vals_out;
+    c.bucket_sizes = bucket_sizes;
+    if (dbg) c.dbg = *dbg;
+    c.stream = (cudaStream_t)stream;
+    BSPS_CUDA(cudaMemsetAsync(c.ly.status, 0, sizeof(DevStatus), c.stream));
+    if (n == 0) {
+        if (bucket_sizes) BSPS_CUDA(cudaMemsetAsync(bucket_sizes, 0, sizeof(int64_t) * c.pl.p, c.stream));
+        if (dbg && dbg->pad_sizes) BSPS_CUDA(cudaMemsetAsync(dbg->pad_sizes, 0, sizeof(int64_t) * c.pl.p, c.stream));
+        return BSPS_OK;
+    }
+    void *const *ev = dbg ? dbg->phase_events : nullptr;
+    auto mark = [&](int i) { return ev ? cudaEventRecord((cudaEvent_t)ev[i], c.stream) : cudaSuccess; };
+    BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
+    BSPS_CUDA(mark(0));
+    BSPS_CUDA(launch_sample(c));
+    BSPS_CUDA(mark(1));
+    BSPS_CUDA(launch_sample_sort(c));
+    BSPS_CUDA(mark(2));
+    BSPS_CUDA(launch_splitters(c));
+    BSPS_CUDA(mark(3));
+    BSPS_CUDA(launch_route(c));
+    BSPS_CUDA(mark(4));
+    BSPS_CUDA(launch_bucket_sort(c));
+    BSPS_CUDA(mark(5));
+    if (dbg) BSPS_CUDA(launch_debug(c));
+    if (dbg && dbg->launches) *dbg->launches = kernels_per_call(c.pl) + debug_kernels(c);
+    return BSPS_OK;
+}
+
+} // namespace bsps
+
+using namespace bsps;
+
+extern "C" {
+
+int bsps_get_plan(int64_t n, int32_t dtype, const bsps_params *prm, int32_t with_payload, bsps_plan *out) {
+    if (!out) return BSPS_ERR_INVALID_ARG;
+    Plan pl;
+    const int rc = make_plan(n, dtype, prm, with_payload != 0, pl);
+    if (rc) return rc;
+    to_public(pl, out);
+    return BSPS_OK;
+}
+
+int bsps_workspace_size(int64_t n, int32_t dtype, const bsps_params *prm, int32_t with_payload, size_t *bytes) {
+    if (!bytes) return BSPS_ERR_INVALID_ARG;
+    Plan pl;
+    const int rc = make_plan(n, dtype, prm, with_payload != 0, pl);
+    if (rc) return rc;
+    *bytes = pl.ws_bytes;
+    return BSPS_OK;
+}
+
+int bsps_sort_keys(const void *d_keys_in, void *d_keys_out, int64_t n, int32_t dtype, const bsps_params *prm,
+                   int64_t *d_bucket_sizes, void *d_ws, size_t ws_bytes, void *stream) {
+    return run(d_keys_in, nullptr, d_keys_out, nullptr, n, dtype, prm, d_bucket_sizes, nullptr, d_ws, ws_bytes,
+               stream);
+}
+
+int bsps_sort_pairs(const void *d_keys_in, const uint32_t *d_vals_in, void *d_keys_out, uint32_t *d_vals_out,
+                    int64_t n, int32_t dtype, const bsps_params *prm, int64_t *d_bucket_sizes, void *d_ws,
+                    size_t ws_bytes, void *stream) {
+    if (n > 0 && (!d_vals_in || !d_vals_out)) return BSPS_ERR_INVALID_ARG;
+    return run(d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, dtype, prm, d_bucket_sizes, nullptr, d_ws,
+               ws_bytes, stream);
+}
+
+int bsps_sort_debug(const void *d_keys_in, const uint32_t *d_vals_in, void *d_keys_out, uint32_t *d_vals_out,
+                    int64_t n, int32_t dtype, const bsps_params *prm, int64_t *d_bucket_sizes,
+                    const bsps_debug *dbg, void *d_ws, size_t ws_bytes, void *stream) {
+    return run(d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, dtype, prm, d_bucket_sizes, dbg, d_ws, ws_bytes,
+               stream);
+}
+
+int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream) {
+    if (!d_ws || !stats) return BSPS_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BSPS_ERR_CUDA;
+    DevStatus st;
+    if (cudaMemcpy(&st, d_ws, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return BSPS_ERR_CUDA;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->status = st.error;
+    stats->overflow = st.overflow;
+    stats->timeouts = st.timeouts;
+    stats->slow_buckets = st.slow_buckets;
+    stats->max_bucket = (int64_t)st.max_bucket;
+    stats->max_vbucket = (int64_t)st.max_vbucket;
+    stats->mispredicted = (int64_t)st.mispredicted;
+    stats->correction_steps = (int64_t)st.correction_steps;
+    return stats->status;
+}
+
+const char *bsps_strerror(int status) {
+    switch (status) {
+    case BSPS_OK: return "ok";
+    case BSPS_ERR_INVALID_ARG: return "invalid argument";
+    case BSPS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case BSPS_ERR_UNSUPPORTED_DTYPE: return "unsupported key type";
+    case BSPS_ERR_BUCKET_OVERFLOW: return "a bucket exceeded its region";
+    case BSPS_ERR_CUDA: return "CUDA error";
+    case BSPS_ERR_DEVICE_TIMEOUT: return "a bounded device wait expired";
+    case BSPS_ERR_TOO_LARGE: return "problem too large for this build";
+    default: return "unknown status";
+    }
+}
+
+} // extern "C"

@@ -1,0 +1,223 @@
+// bucket.cu -- final sort of every bucket (Fig. 2 step 12 / Fig. 3 step 14):
+// the keys a bucket received, in input order, are sorted stably and written
+// to the bucket's place in the output.  Each sub-bucket is sorted on chip by
+// one thread-block cluster; sub-buckets larger than the cluster's shared
+// memory go to an out-of-core radix sort in global memory.
+#include "kernels.cuh"
+#include "radix.cuh"
+
+namespace bsps {
+
+template <typename K> struct BucketArgs {
+    const K *reg_keys;        // phi of the routed keys, region v at v*cap
+    const uint32_t *reg_vals;
+    const uint32_t *vsize;
+    const uint64_t *voff;
+    int64_t cap;
+    K *out_keys;
+    uint32_t *out_vals;
+    uint32_t *slow_list;
+    DevStatus *st;
+};
+
+template <int DT, bool PAIRS, int CL, int ITEMS>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSortThreads, 1)
+bucket_sort_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
+    using K = typename KeyTraits<DT>::T;
+    using CS = ClusterSort<K, PAIRS, kSortThreads, ITEMS, CL>;
+    constexpr int CAP = CS::CAP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename CS::Smem &sm = *reinterpret_cast<typename CS::Smem *>(smem_raw);
+    K *kbuf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename CS::Smem) + 15) & ~size_t(15)));
+    uint32_t *vbuf = reinterpret_cast<uint32_t *>(kbuf + CAP);
+
+    auto cluster = cg::this_cluster();
+    const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
+    const int64_t v = blockIdx.x / CL;
+    const int64_t cnt = imin64(a.vsize[v], a.cap);
+    if (cnt == 0) return;
+    if (cnt > (int64_t)CL * CAP) {  // whole cluster leaves together
+        if (rank == 0 && threadIdx.x == 0) {
+            const int slot = atomicAdd(&a.st->slow_buckets, 1);
+            a.slow_list[slot] = (uint32_t)v;
+        }
+        return;
+    }
+    const K *src = a.reg_keys + v * a.cap;
+    K mn = all_ones<K>(), mx = 0;
+    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
+        const int64_t e = (int64_t)rank * CAP + t;
+        K x = all_ones<K>();
+        if (e < cnt) {
+            x = src[e];
+            mn = x < mn ? x : mn;
+            mx = x > mx ? x : mx;
+        }
+        kbuf[t] = x;
+        if constexpr (PAIRS) vbuf[t] = (uint32_t)e;
+    }
+    K base, top;
+    CS::minmax(sm, mn, mx, base, top);
+    const int bits = bit_length<K>(top - base);
+    if (bits > 0) {
+        for (int t = threadIdx.x; t < CAP; t += kSortThreads)
+            if ((int64_t)rank * CAP + t < cnt) kbuf[t] -= base;
+        __syncthreads();
+        CS::sort(sm, kbuf, vbuf, bits);
+    }
+    const uint64_t off = a.voff[v];
+    const int k_add = bits > 0;
+    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
+        const int64_t pos = (int64_t)rank * CAP + t;
+        if (pos < cnt) {
+            const K x = k_add ? kbuf[t] + base : kbuf[t];
+            a.out_keys[off + pos] = KeyTraits<DT>::inv(x);
+            if constexpr (PAIRS) a.out_vals[off + pos] = a.reg_vals[v * a.cap + vbuf[t]];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Out-of-core path: one CTA sorts one oversized sub-bucket by LSD passes
+// between its region and its output range, chunk by chunk, stably.
+// ---------------------------------------------------------------------------
+template <int DT, bool PAIRS>
+__global__ void __launch_bounds__(kSlowThreads) bucket_slow_kernel(BucketArgs<typename KeyTraits<DT>::T> a,
+                                                                  typename KeyTraits<DT>::T *reg_keys_rw,
+                                                                  uint32_t *reg_vals_rw) {
+    using K = typename KeyTraits<DT>::T;
+    using Rank = BlockRank<kSlowThreads, kSlowItems, 8>;
+    constexpr int CH = kSlowThreads * kSlowItems;
+    __shared__ typename Rank::Smem rsm;
+    __shared__ uint32_t hist[256], run[256], tmp[40];
+    __shared__ K red[2];
+    const int nslow = a.st->slow_buckets;
+    for (int idx = blockIdx.x; idx < nslow; idx += gridDim.x) {
+        const int64_t v = a.slow_list[idx];
+        const int64_t cnt = imin64(a.vsize[v], a.cap);
+        const uint64_t off = a.voff[v];
+        K *bufk[2] = {reg_keys_rw + v * a.cap, reinterpret_cast<K *>(a.out_keys) + off};
+        uint32_t *bufv[2] = {PAIRS ? reg_vals_rw + v * a.cap : nullptr, PAIRS ? a.out_vals + off : nullptr};
+        // key range
+        K mn = all_ones<K>(), mx = 0;
+        for (int64_t e = threadIdx.x; e < cnt; e += kSlowThreads) {
+            const K x = bufk[0][e];
+            mn = x < mn ? x : mn;
+            mx = x > mx ? x : mx;
+        }
+        if (threadIdx.x == 0) { red[0] = all_ones<K>(); red[1] = 0; }
+        __syncthreads();
+        if constexpr (sizeof(K) == 8) {
+            atomicMin((unsigned long long *)&red[0], (unsigned long long)mn);
+            atomicMax((unsigned long long *)&red[1], (unsigned long long)mx);
+        } else {
+            atomicMin((unsigned *)&red[0], (unsigned)mn);
+            atomicMax((unsigned *)&red[1], (unsigned)mx);
+        }
+        __syncthreads();
+        const K base = red[0];
+        const int bits = bit_length<K>(red[1] - base);
+        __syncthreads();
+        int cur = 0;
+        for (int shift = 0; shift < bits; shift += 8) {
+            const K *sk = bufk[cur];
+            K *dk = bufk[1 - cur];
+            for (int i = threadIdx.x; i < 256; i += kSlowThreads) { hist[i] = 0; }
+            __syncthreads();
+            for (int64_t e = threadIdx.x; e < cnt; e += kSlowThreads)
+                atomicAdd(&hist[(uint32_t)((sk[e] - base) >> shift) & 255u], 1u);
+            __syncthreads();
+            digit_excl_scan<kSlowThreads, 256>(hist, tmp);
+            for (int i = threadIdx.x; i < 256; i += kSlowThreads) run[i] = hist[i];
+            __syncthreads();
+            for (int64_t cs = 0; cs < cnt; cs += CH) {
+                K kk[kSlowItems];
+                uint32_t vv[kSlowItems], d[kSlowItems], rk[kSlowItems];
+#pragma unroll
+                for (int i = 0; i < kSlowItems; ++i) {
+                    const int64_t e = cs + striped_slot<kSlowThreads, kSlowItems>(i);
+                    if (e < cnt) {
+                        kk[i] = sk[e];
+                        if constexpr (PAIRS) vv[i] = bufv[cur][e];
+                        d[i] = (uint32_t)((kk[i] - base) >> shift) & 255u;
+                    } else {
+                        d[i] = 255u;
+                    }
+                }
+                Rank::rank(rsm, d, rk);
+#pragma unroll
+                for (int i = 0; i < kSlowItems; ++i) {
+                    const int64_t e = cs + striped_slot<kSlowThreads, kSlowItems>(i);
+                    if (e < cnt) {
+                        const uint32_t pos = run[d[i]] + rk[i];
+                        dk[pos] = kk[i];
+                        if constexpr (PAIRS) bufv[1 - cur][pos] = vv[i];
+                    }
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < 256; i += kSlowThreads) run[i] += rsm.digit_tot[i];
+                __syncthreads();
+            }
+            cur = 1 - cur;
+        }
+        // final placement in the output, back to key bits
+        for (int64_t e = threadIdx.x; e < cnt; e += kSlowThreads) {
+            const K x = bufk[cur][e];
+            if constexpr (PAIRS) {
+                if (cur == 0) a.out_vals[off + e] = bufv[0][e];
+            }
+            a.out_keys[off + e] = KeyTraits<DT>::inv(x);
+        }
+        __syncthreads();
+    }
+}
+
+template <int DT, bool PAIRS, int CL, int ITEMS> static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
+    using K = typename KeyTraits<DT>::T;
+    using CS = ClusterSort<K, PAIRS, kSortThreads, ITEMS, CL>;
+    const size_t smem = ((sizeof(typename CS::Smem) + 15) & ~size_t(15)) + CS::CAP * (sizeof(K) + (PAIRS ? 4 : 0));
+    auto kern = bucket_sort_kernel<DT, PAIRS, CL, ITEMS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(c.pl.P * CL), kSortThreads, smem, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
+    using K = typename KeyTraits<DT>::T;
+    BucketArgs<K> a;
+    a.reg_keys = (const K *)c.ly.reg_keys;
+    a.reg_vals = c.ly.reg_vals;
+    a.vsize = c.ly.vsize;
+    a.voff = c.ly.voff;
+    a.cap = c.pl.cap;
+    a.out_keys = (K *)c.keys_out;
+    a.out_vals = c.vals_out;
+    a.slow_list = c.ly.slow_list;
+    a.st = c.ly.status;
+    constexpr int IT = PAIRS ? (sizeof(K) == 8 ? kPairItems64 : kPairItems32)
+                             : (sizeof(K) == 8 ? kBucketItems64 : kBucketItems32);
+    cudaError_t e;
+    switch (c.pl.bucket_cl) {
+    case 1: e = launch_cluster<DT, PAIRS, 1, IT>(c, a); break;
+    case 2: e = launch_cluster<DT, PAIRS, 2, IT>(c, a); break;
+    case 4: e = launch_cluster<DT, PAIRS, 4, IT>(c, a); break;
+    case 8: e = launch_cluster<DT, PAIRS, 8, IT>(c, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    bucket_slow_kernel<DT, PAIRS><<<64, kSlowThreads, 0, c.stream>>>(a, (K *)c.ly.reg_keys, c.ly.reg_vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_sort(const Ctx &c) {
+    const bool pr = c.pl.pairs != 0;
+    switch (c.pl.dtype) {
+    case BSPS_U32: return pr ? launch_bucket_t<BSPS_U32, true>(c) : launch_bucket_t<BSPS_U32, false>(c);
+    case BSPS_I32: return pr ? launch_bucket_t<BSPS_I32, true>(c) : launch_bucket_t<BSPS_I32, false>(c);
+    case BSPS_F32: return pr ? launch_bucket_t<BSPS_F32, true>(c) : launch_bucket_t<BSPS_F32, false>(c);
+    default: return pr ? launch_bucket_t<BSPS_F64, true>(c) : launch_bucket_t<BSPS_F64, false>(c);
+    }
+}
+
+} // namespace bsps

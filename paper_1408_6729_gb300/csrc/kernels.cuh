@@ -1,0 +1,113 @@
+// kernels.cuh -- the plan of one sort call, the workspace layout, and the
+// host-side launchers of each step of the path.
+#pragma once
+
+#include "common.cuh"
+
+namespace bsps {
+
+// Number of cells of the radix index placed in front of the splitter tree.
+constexpr int kLutBits = 13;
+constexpr int kLutCells = 1 << kLutBits;
+
+// Routing geometry (Fig. 1 steps 9-11).
+constexpr int kRouteThreads = 512;
+constexpr int kRouteItems = 8;                              // keys per thread per chunk
+constexpr int kRouteChunk = kRouteThreads * kRouteItems;    // keys staged in shared memory
+constexpr int kRouteChunksPerTile = 16;
+constexpr int kRouteTile = kRouteChunk * kRouteChunksPerTile;  // keys per lookback tile
+
+// Sample-sort geometry (Fig. 1 step 5).
+constexpr int kLsdThreads = 512;
+constexpr int kLsdItems = 16;
+constexpr int kLsdTile = kLsdThreads * kLsdItems;
+
+// Bucket / block sort geometry (Fig. 1 step 3, Fig. 2 step 12).
+constexpr int kSortThreads = 512;
+constexpr int kRunItems32 = 16;        // block sort with input-slot companion, 4-byte keys
+constexpr int kRunItems64 = 12;        // ... 8-byte keys
+constexpr int kBucketItems32 = 32;     // sub-bucket sort, keys only, 4-byte keys
+constexpr int kBucketItems64 = 16;     // ... 8-byte keys
+constexpr int kPairItems32 = 16;       // sub-bucket sort with payload slots, 4-byte keys
+constexpr int kPairItems64 = 12;       // ... 8-byte keys
+constexpr int kSlowThreads = 512;      // out-of-core sort of an oversized sub-bucket
+constexpr int kSlowItems = 8;
+
+// Where the radix index sends a key: cells of width 2^shift above `base`.
+template <typename K> struct LutParams {
+    K base;        // phi of the smallest splitter
+    K span;        // phi(largest splitter) - base
+    uint32_t shift;
+    uint32_t nsplit; // number of splitters (vbuckets - 1)
+};
+
+template <typename K> struct LsdBuffers {
+    K *phi[2];
+    uint32_t *tag[2];
+};
+
+struct Plan {
+    int64_t n, p, R, s, m, M, x, q, sample_size;
+    int sampling, dtype, pairs, classify;
+    uint64_t seed;
+    int64_t B;         // refine: sub-buckets per bucket
+    int64_t P;         // vbuckets = p * B
+    int64_t Q;         // sample records between consecutive splitters (q or s)
+    int64_t cap;       // keys per sub-bucket region
+    int run_cl;        // cluster size of the block sort (regular sampling)
+    int bucket_cl;     // cluster size of the sub-bucket sort
+    int64_t tiles;     // routing tiles
+    int64_t lsd_tiles; // sample-sort tiles
+    int lsd_npos;      // radix digit positions of a sample record
+    int key_bytes;
+    size_t ws_bytes;
+};
+
+// Device pointers into the caller's workspace (all 256-byte aligned).
+struct Layout {
+    DevStatus *status;
+    void *sphi[2];          // sample record phi (ping-pong), key width
+    uint32_t *stag[2];      // sample record tag (ping-pong)
+    uint32_t *lsd_counts;   // lsd_tiles * 256
+    uint32_t *lsd_hist;     // lsd_npos * 256
+    int32_t *lsd_table;     // pass table of the sample sort
+    void *vphi;             // P-1 sub-bucket splitters, phi
+    uint32_t *vtag;         // P-1 sub-bucket splitters, tag
+    uint32_t *lut;          // kLutCells + 1
+    void *lutp;             // LutParams<K>
+    uint32_t *state;        // tiles * P lookback words
+    void *reg_keys;         // P * cap keys (phi), region v at v*cap
+    uint32_t *reg_vals;     // P * cap payloads
+    uint32_t *vsize;        // P sub-bucket sizes
+    uint64_t *voff;         // P + 1 exclusive offsets
+    uint32_t *slow_list;    // sub-buckets too large for the on-chip sort
+};
+
+struct Ctx {
+    Plan pl;
+    Layout ly;
+    const void *keys_in;
+    const uint32_t *vals_in;
+    void *keys_out;
+    uint32_t *vals_out;
+    int64_t *bucket_sizes;
+    bsps_debug dbg;
+    cudaStream_t stream;
+};
+
+// Internal record tag: the input position g for a key, n + k*M + j for the
+// pad at local index j of virtual processor k; phi of a pad is all ones.
+// (pad, phi, k*M+j) order == (phi', tag') order with these encodings.
+
+// launchers (each returns cudaSuccess or the launch error)
+cudaError_t launch_sample(const Ctx &c);          // Fig. 1 steps 3-4 / Fig. 3 step 4
+cudaError_t launch_sample_sort(const Ctx &c);     // Fig. 1 step 5
+cudaError_t launch_splitters(const Ctx &c);       // Fig. 1 steps 6-7
+cudaError_t launch_route(const Ctx &c);           // Fig. 1 steps 9-11
+cudaError_t launch_bucket_sort(const Ctx &c);     // Fig. 2 step 12
+cudaError_t launch_debug(const Ctx &c);           // optional diagnostics
+
+// Byte counts of dynamic shared memory (host side).
+size_t route_smem_bytes(const Plan &pl);
+
+} // namespace bsps

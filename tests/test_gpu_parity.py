@@ -1,0 +1,164 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Compared bit for bit: sorted keys, payloads, bucket sizes, splitters (phi, tag,
+pad), the sorted sample, per-key buckets (n <= 2^22) and pad counts.  Sizes span
+several routing tiles (65536 keys), chunks (4096 keys) and cluster slots, with
+ragged tails; the edge cases are n = 0, 1, p-1, p, p+1, p = 1, all-equal keys,
+buckets larger than one cluster's shared memory (out-of-core path) and a bucket
+region too small on purpose (overflow is reported, nothing is written past it).
+"""
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bsp_inputs as gen
+import oracle
+from tests.gpu_util import assert_same, run_gpu
+from tests.test_oracle import GOLDEN, _as_keys
+
+pytestmark = pytest.mark.gpu
+
+MODES = [oracle.REGULAR, oracle.RANDOM]
+MODE_IDS = ["regular", "random"]
+
+
+def ref_sort(keys, p, s=0, runs=0, mode=0, seed=0, vals=None):
+    return oracle.sort(keys, p, s, runs, mode, seed, vals=vals, want_bucket_of=keys.shape[0] <= (1 << 22))
+
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "*.json"))),
+                         ids=lambda p: os.path.basename(p))
+def test_golden_hand_worked_on_gpu(path):
+    g = json.load(open(path))
+    keys = _as_keys(g["keys"], g["dtype"])
+    vals = np.array(g["vals"], np.uint32)
+    r = run_gpu(keys, g["p"], g["s"], g["runs"], oracle.REGULAR, vals=vals)
+    assert r.stats.status == 0
+    assert r.keys.tobytes() == _as_keys(g["sorted_keys"], g["dtype"]).tobytes()
+    assert r.vals.tolist() == g["sorted_vals"]
+    assert r.bucket_sizes.tolist() == g["bucket_sizes"]
+    assert r.pad_sizes.tolist() == g["pad_sizes"]
+    assert r.bucket_of.tolist() == g["bucket_of"]
+    assert [[int(x["phi"]), int(x["tag"]), int(x["pad"])] for x in r.splitters] == \
+        [[int(a, 16), b, c] for a, b, c in g["splitters"]]
+    assert [[int(x["phi"]), int(x["tag"]), int(x["pad"])] for x in r.sample] == \
+        [[int(a, 16), b, c] for a, b, c in g["sample"]]
+
+
+DTYPE_KEYS = {
+    "i32": lambda n, p, seed: gen.uniform(n, p, seed),
+    "u32": lambda n, p, seed: gen.uniform_u32(n, seed),
+    "f32": lambda n, p, seed: gen.gmm(n, seed=seed).astype(np.float32),
+    "f64": lambda n, p, seed: gen.gmm(n, seed=seed),
+}
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("dt", sorted(DTYPE_KEYS))
+@pytest.mark.parametrize("n,p", [(1, 4), (3, 4), (4, 4), (5, 4), (1000, 7), (65537, 16), (300_001, 64)])
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+def test_edge_sizes_and_dtypes(mode, dt, n, p, pairs):
+    keys = DTYPE_KEYS[dt](n, p, 5)
+    vals = np.arange(n, dtype=np.uint32)[::-1].copy() if pairs else None
+    s = 0
+    try:
+        ref = ref_sort(keys, p, s, 0, mode, 9, vals)
+    except ValueError:
+        pytest.skip("parameters invalid for this n")
+    gpu = run_gpu(keys, p, s, 0, mode, 9, vals)
+    assert_same(gpu, ref)
+
+
+def test_empty_input():
+    keys = np.zeros(0, np.int32)
+    r = run_gpu(keys, 8, debug=False)
+    assert r.stats.status == 0
+    assert r.keys.shape == (0,)
+    assert r.bucket_sizes.tolist() == [0] * 8
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_single_bucket(mode):
+    keys = gen.gaussian(100_000, 4, 3)
+    ref = ref_sort(keys, 1, 0, 4 if mode == oracle.REGULAR else 0, mode, 5)
+    gpu = run_gpu(keys, 1, 0, 4 if mode == oracle.REGULAR else 0, mode, 5)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("name", sorted(gen.DISTRIBUTIONS))
+def test_distributions_2e20(mode, name):
+    n, p = 1 << 20, 256
+    keys = gen.DISTRIBUTIONS[name](n, p, 1)
+    vals = np.arange(n, dtype=np.uint32)
+    ref = ref_sort(keys, p, 0, 0, mode, 21, vals)
+    gpu = run_gpu(keys, p, 0, 0, mode, 21, vals)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("s", [8, 512], ids=["s8_literal", "s512"])
+def test_config1_regular_u32_2e20(s):
+    """n = 2^20 uint32 uniform on [0, 2^32), p = 64, R = 64, regular oversampling."""
+    keys = gen.uniform_u32(1 << 20, seed=1)
+    ref = ref_sort(keys, 64, s, 64, oracle.REGULAR)
+    gpu = run_gpu(keys, 64, s, 64, oracle.REGULAR)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("refine", [1, 2, 4])
+def test_refinement_changes_nothing(refine):
+    keys = gen.uniform(1 << 21, 256, 2)
+    ref = ref_sort(keys, 256, 0, 0, oracle.RANDOM, 4)
+    gpu = run_gpu(keys, 256, 0, 0, oracle.RANDOM, 4, refine=refine)
+    assert_same(gpu, ref)
+    assert gpu.plan.vbuckets == 256 * refine
+
+
+def test_zipf_pairs_regular_duplicates():
+    """Duplicate-heavy pairs with the tag-free tie-break (Sec. 5.1.1), regular mode."""
+    n, p = 1 << 22, 256
+    keys = gen.zipf(n, seed=3)
+    vals = np.arange(n, dtype=np.uint32)
+    ref = ref_sort(keys, p, p, p, oracle.REGULAR, 0, vals)
+    gpu = run_gpu(keys, p, p, p, oracle.REGULAR, 0, vals)
+    assert_same(gpu, ref)
+
+
+def test_gmm_f64_random_small_sample():
+    n, p = 1 << 22, 4096
+    keys = gen.gmm(n, seed=4)
+    ref = ref_sort(keys, p, 16, 0, oracle.RANDOM, 8)
+    gpu = run_gpu(keys, p, 16, 0, oracle.RANDOM, 8)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+def test_out_of_core_bucket_path(pairs):
+    """Buckets far larger than one cluster's shared memory."""
+    n, p = 600_000, 2
+    keys = gen.gaussian(n, p, 8)
+    vals = np.arange(n, dtype=np.uint32) if pairs else None
+    ref = ref_sort(keys, p, 0, 0, oracle.RANDOM, 3, vals)
+    gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 3, vals, refine=1)
+    assert gpu.stats.slow_buckets > 0
+    assert_same(gpu, ref)
+
+
+def test_overflow_is_reported_not_written():
+    keys = gen.uniform(200_000, 16, 2)
+    gpu = run_gpu(keys, 16, 0, 0, oracle.RANDOM, 3, capacity_pct=60, debug=False)
+    assert gpu.stats.overflow == 1
+    assert gpu.stats.status == -4  # BSPS_ERR_BUCKET_OVERFLOW
+
+
+@pytest.mark.parametrize("name", sorted(gen.DISTRIBUTIONS))
+def test_config2_random_2e26(name):
+    """n = 2^26 int32, random oversampling, p = 1024, the five seeded inputs."""
+    n, p = 1 << 26, 1024
+    keys = gen.DISTRIBUTIONS[name](n, p, 1)
+    ref = oracle.sort(keys, p, 0, 0, oracle.RANDOM, 1, want_sample=True)
+    gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 1, bucket_of=False)
+    assert_same(gpu, ref)
