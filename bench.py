@@ -41,6 +41,10 @@ WORKLOADS = {
                                             make=lambda n, p, seed: gen.uniform(n, p, seed)),
     "zipf_2e28_int32_pairs_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=True,
                                                make=lambda n, p, seed: gen.zipf(n, seed=seed)),
+    # the 2^26 / p = 1024 shape of the randomized config: same bucket sizes, a
+    # quarter of the data (used for profiling captures)
+    "uniform_2e26_int32_p1024_random": dict(n=1 << 26, p=1024, sampling=1, s=0, runs=0, pairs=False,
+                                           make=lambda n, p, seed: gen.uniform(n, p, seed)),
 }
 DEFAULT_WORKLOAD = "uniform_2e28_int32_p4096_random"
 METRIC = "keys/sec and % HBM roofline, 2^28 int32; learned/batched vs plain, bit-exact"
@@ -261,6 +265,22 @@ def run_gpu(args, wl, name):
 
     # end to end through the C ABI with host buffers: H2D of the keys, the sort,
     # D2H of the sorted keys, every step
+    if args.no_e2e:
+        e2e_ms, e2e_steps = float("nan"), 0
+    else:
+        e2e_ms, e2e_steps = run_e2e(args, stream, kin, kout, keys_h, step, pg, n)
+    if rank != 0:
+        return
+    return report(args, wl, name, world, n, p, plan, st, per_step_of(phase_ms, args), elapsed_ms, e2e_ms,
+                  e2e_steps, total_launches, clk)
+
+
+def per_step_of(phase_ms, args):
+    return {k: v / args.steps for k, v in phase_ms.items()}
+
+
+def run_e2e(args, stream, kin, kout, keys_h, step, pg, n):
+    import torch
     h_in = torch.from_numpy(keys_h).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
@@ -280,12 +300,12 @@ def run_gpu(args, wl, name):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(pg, e0.elapsed_time(e1))
     assert np.array_equal(h_out.numpy()[:: max(1, n // 4096)], kout.cpu().numpy()[:: max(1, n // 4096)])
+    return e2e_ms, e2e_steps
 
-    if rank != 0:
-        return
+
+def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, e2e_steps, total_launches, clk):
     pk, pk_kind = peaks()
     kb = 4 + (4 if wl["pairs"] else 0)
-    per_step = {k: v / args.steps for k, v in phase_ms.items()}
     dom = max(("route", "bucket_sort"), key=lambda k: per_step[k])
     kern = PHASE_KERNEL[dom]
     alg_bytes = n * 2 * kb
@@ -297,7 +317,7 @@ def run_gpu(args, wl, name):
     value = world * n / (ms_step * 1e-3)
     b_alg = 4 * kb + plan.sample_size * (4 + 8) / n + (kb if wl["sampling"] == 0 else 0)
     cpu = None
-    if world == 1:
+    if world == 1 and not args.no_baseline:
         rate, ns, s_used, runs_used, t_used = oracle_rate(wl)
         cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"{ns} keys of the same generator, p={p}, s={s_used}, "
@@ -318,8 +338,8 @@ def run_gpu(args, wl, name):
                           "frac": n * b_alg / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"]},
         "phases_ms": per_step,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "keys/s",
-                "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+        "e2e": None if args.no_e2e else {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "keys/s",
+                                         "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
         "gpu_launches": total_launches,
         "clocks": clk.summary(),
         "stats": {"max_bucket": st.max_bucket, "max_vbucket": st.max_vbucket, "slow_buckets": st.slow_buckets,
@@ -335,6 +355,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

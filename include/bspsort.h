@@ -137,6 +137,8 @@ typedef struct {
     int64_t *pad_sizes;      /* p pad counts (regular mode) */
     void *const *phase_events;
     int32_t *launches;
+    float *mlp_params;       /* learned classifier: the 1153 trained parameters */
+    float *mlp_loss;         /* learned classifier: training loss before and after */
 } bsps_debug;
 
 /*
@@ -190,6 +192,22 @@ int bsps_sort_debug(const void *d_keys_in, const uint32_t *d_vals_in, void *d_ke
  * Returns stats->status.
  */
 int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream);
+
+/*
+ * Learned classifier (params.classify = BSPS_LEARNED; not in the paper).  A
+ * 1->32->32->1 ReLU network (FP32) is trained on the sample the method draws
+ * (the empirical CDF of the sorted sample), predicts each key's sub-bucket as
+ * floor(P * y), and a bounded search against the true splitters corrects every
+ * prediction, so all results equal those of BSPS_TREE.  Parameters are packed
+ * as W1[32] b1[32] W2[32][32] (row i = unit i of layer 2) b2[32] w3[32] b3.
+ *
+ * bsps_mlp_loss_grad -- mean squared error of the network `d_params` on the m
+ * points (d_x[i], d_y[i]) and its gradient (1153 floats into d_grad; loss into
+ * d_loss, nullable).  Workspace: bsps_mlp_workspace_size(m) bytes.
+ */
+int bsps_mlp_workspace_size(int64_t m, size_t *bytes);
+int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y, int64_t m, float *d_grad,
+                       float *d_loss, void *d_ws, size_t ws_bytes, void *stream);
 
 /* bsps_strerror -- static text for a status code. */
 const char *bsps_strerror(int status);

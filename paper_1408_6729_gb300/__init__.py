@@ -26,7 +26,9 @@ BSPS_ERR_DEVICE_TIMEOUT = -6
 BSPS_ERR_TOO_LARGE = -7
 
 EXPORTS = ["bsps_get_plan", "bsps_workspace_size", "bsps_sort_keys", "bsps_sort_pairs",
-           "bsps_sort_debug", "bsps_read_stats", "bsps_strerror"]
+           "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad",
+           "bsps_strerror"]
+MLP_PARAMS = 1153
 
 
 class bsps_params(ctypes.Structure):
@@ -62,7 +64,8 @@ class bsps_debug(ctypes.Structure):
     _fields_ = [("sample", ctypes.c_void_p), ("splitters", ctypes.c_void_p),
                 ("bucket_of", ctypes.c_void_p), ("pad_sizes", ctypes.c_void_p),
                 ("phase_events", ctypes.POINTER(ctypes.c_void_p)),
-                ("launches", ctypes.POINTER(ctypes.c_int32))]
+                ("launches", ctypes.POINTER(ctypes.c_int32)),
+                ("mlp_params", ctypes.c_void_p), ("mlp_loss", ctypes.c_void_p)]
 
 
 _lib = None
@@ -85,10 +88,13 @@ def load(path: str = LIB_PATH):
     lib.bsps_sort_pairs.argtypes = [P, P, P, P, I64, I32, PP, P, P, SZ, P]
     lib.bsps_sort_debug.argtypes = [P, P, P, P, I64, I32, PP, P, ctypes.POINTER(bsps_debug), P, SZ, P]
     lib.bsps_read_stats.argtypes = [P, ctypes.POINTER(bsps_stats), P]
+    lib.bsps_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
+    lib.bsps_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, SZ, P]
     lib.bsps_strerror.argtypes = [ctypes.c_int]
     lib.bsps_strerror.restype = ctypes.c_char_p
-    for name in EXPORTS[:-1]:
-        getattr(lib, name).restype = ctypes.c_int
+    for name in EXPORTS:
+        if name != "bsps_strerror":
+            getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -165,10 +171,11 @@ def bsps_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, dtype, params, buck
 
 def bsps_sort_debug(keys_in, vals_in, keys_out, vals_out, n, dtype, params, bucket_sizes, workspace,
                     sample=None, splitters=None, bucket_of=None, pad_sizes=None, phase_events=None,
-                    launches=None, stream=None) -> int:
+                    launches=None, mlp_params=None, mlp_loss=None, stream=None) -> int:
     """phase_events: BSPS_PHASES recorded torch.cuda.Event objects (or raw handles);
     launches: a ctypes.c_int32 that receives the number of kernels launched."""
-    dbg = bsps_debug(_ptr(sample), _ptr(splitters), _ptr(bucket_of), _ptr(pad_sizes), None, None)
+    dbg = bsps_debug(_ptr(sample), _ptr(splitters), _ptr(bucket_of), _ptr(pad_sizes), None, None,
+                     _ptr(mlp_params), _ptr(mlp_loss))
     if phase_events is not None:
         handles = [e if isinstance(e, int) else e.cuda_event for e in phase_events]
         assert len(handles) == BSPS_PHASES and all(handles), "events must exist (record them once first)"
@@ -178,6 +185,19 @@ def bsps_sort_debug(keys_in, vals_in, keys_out, vals_out, n, dtype, params, buck
     return load().bsps_sort_debug(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), int(n),
                                   int(dtype), ctypes.byref(params), _ptr(bucket_sizes), ctypes.byref(dbg),
                                   _ptr(workspace), _nbytes(workspace), _stream(stream))
+
+
+def bsps_mlp_workspace_size(m) -> int:
+    out = ctypes.c_size_t()
+    rc = load().bsps_mlp_workspace_size(int(m), ctypes.byref(out))
+    if rc:
+        raise ValueError(f"bsps_mlp_workspace_size: {bsps_strerror(rc)} ({rc})")
+    return out.value
+
+
+def bsps_mlp_loss_grad(params, x, y, m, grad, loss, workspace, stream=None) -> int:
+    return load().bsps_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), int(m), _ptr(grad), _ptr(loss),
+                                     _ptr(workspace), _nbytes(workspace), _stream(stream))
 
 
 def bsps_read_stats(workspace, stream=None) -> bsps_stats:

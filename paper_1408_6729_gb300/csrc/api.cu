@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "kernels.cuh"
+#include "mlp.cuh"
 
 namespace bsps {
 
@@ -68,7 +69,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         pl.Q = pl.s;
         pl.sample_size = pl.s * pl.p - 1;
     }
-    if (pl.sample_size >= ((int64_t)1 << 31) || pl.p > ((int64_t)1 << 24)) return BSPS_ERR_TOO_LARGE;
+    if (pl.sample_size >= ((int64_t)1 << 31) || pl.p > 65535) return BSPS_ERR_TOO_LARGE;
 
     // sub-buckets: the smallest refinement whose expected size fits one
     // cluster's shared memory with head room for the sampling imbalance
@@ -85,6 +86,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     if (B > pl.Q) return BSPS_ERR_INVALID_ARG;
     pl.B = B;
     pl.P = pl.p * B;
+    if (pl.P > 65535) return BSPS_ERR_TOO_LARGE;  // 16-bit sub-bucket ids
     const double expect = (double)n / pl.P * headroom(B);
     pl.bucket_cl = 8;
     for (int cl = 1; cl <= 8; cl *= 2)
@@ -125,14 +127,23 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(64 * 4);
     take(pl.P * pl.key_bytes);
     take(pl.P * 4);
-    take((kLutCells + 2) * 4);
+    take((kLutCells + 2) * 2);
     take(64);
     take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
+    take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
+    take(pl.P * 4);
     take(pl.P * pl.cap * pl.key_bytes);
     take(pairs ? pl.P * pl.cap * 4 : 0);
     take(pl.P * 4);
     take((pl.P + 1) * 8);
     take(pl.P * 4);
+    if (pl.classify == BSPS_LEARNED) {
+        take(kParams * 4); take(kParams * 4); take(kParams * 4);
+        take((int64_t)kMlpGridMax * (kParams + 1) * 4);
+        take(kMlpPointsMax * 4); take(kMlpPointsMax * 4);
+        take(8);
+        take(sizeof(MlpNorm));
+    }
     pl.ws_bytes = (size_t)o;
     return BSPS_OK;
 }
@@ -153,14 +164,30 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.lsd_table = (int32_t *)take(64 * 4);
     l.vphi = take(pl.P * pl.key_bytes);
     l.vtag = (uint32_t *)take(pl.P * 4);
-    l.lut = (uint32_t *)take((kLutCells + 2) * 4);
+    l.lut = (uint16_t *)take((kLutCells + 2) * 2);
     l.lutp = take(64);
     l.state = (uint32_t *)take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
+    l.ids = (uint16_t *)take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
+    l.cursor = (uint32_t *)take(pl.P * 4);
     l.reg_keys = take(pl.P * pl.cap * pl.key_bytes);
     l.reg_vals = (uint32_t *)take(pl.pairs ? pl.P * pl.cap * 4 : 0);
     l.vsize = (uint32_t *)take(pl.P * 4);
     l.voff = (uint64_t *)take((pl.P + 1) * 8);
     l.slow_list = (uint32_t *)take(pl.P * 4);
+    if (pl.classify == BSPS_LEARNED) {
+        l.mlp_params = (float *)take(kParams * 4);
+        l.mlp_m = (float *)take(kParams * 4);
+        l.mlp_v = (float *)take(kParams * 4);
+        l.mlp_part = (float *)take((int64_t)kMlpGridMax * (kParams + 1) * 4);
+        l.mlp_x = (float *)take(kMlpPointsMax * 4);
+        l.mlp_y = (float *)take(kMlpPointsMax * 4);
+        l.mlp_npts = (int64_t *)take(8);
+        l.mlp_norm = (MlpNorm *)take(sizeof(MlpNorm));
+    } else {
+        l.mlp_params = l.mlp_m = l.mlp_v = l.mlp_part = l.mlp_x = l.mlp_y = nullptr;
+        l.mlp_npts = nullptr;
+        l.mlp_norm = nullptr;
+    }
     return l;
 }
 
@@ -180,6 +207,7 @@ static int kernels_per_call(const Plan &pl) {
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
     k += 2;                                      // cluster bucket sort, out-of-core bucket sort
+    if (pl.classify == BSPS_LEARNED) k += 3;     // training set, initial weights, training
     return k;
 }
 
@@ -206,7 +234,6 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     const int pairs = vals_in != nullptr;
     int rc = make_plan(n, dtype, prm, pairs, c.pl);
     if (rc) return rc;
-    if (c.pl.classify == BSPS_LEARNED) return BSPS_ERR_INVALID_ARG;  // see bsps_sort_learned
     if (pairs && !vals_out) return BSPS_ERR_INVALID_ARG;
     if (n > 0 && (!keys_in || !keys_out)) return BSPS_ERR_INVALID_ARG;
     if (n > 0 && keys_in == keys_out) return BSPS_ERR_INVALID_ARG;
@@ -229,13 +256,15 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     }
     void *const *ev = dbg ? dbg->phase_events : nullptr;
     auto mark = [&](int i) { return ev ? cudaEventRecord((cudaEvent_t)ev[i], c.stream) : cudaSuccess; };
-    BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
+    if (c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
+    BSPS_CUDA(cudaMemsetAsync(c.ly.cursor, 0, (size_t)c.pl.P * 4, c.stream));
     BSPS_CUDA(mark(0));
     BSPS_CUDA(launch_sample(c));
     BSPS_CUDA(mark(1));
     BSPS_CUDA(launch_sample_sort(c));
     BSPS_CUDA(mark(2));
     BSPS_CUDA(launch_splitters(c));
+    if (c.pl.classify == BSPS_LEARNED) BSPS_CUDA(launch_mlp_train(c));
     BSPS_CUDA(mark(3));
     BSPS_CUDA(launch_route(c));
     BSPS_CUDA(mark(4));

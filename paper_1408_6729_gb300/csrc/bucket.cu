@@ -4,7 +4,7 @@
 // one thread-block cluster; sub-buckets larger than the cluster's shared
 // memory go to an out-of-core radix sort in global memory.
 #include "kernels.cuh"
-#include "radix.cuh"
+#include "segsort.cuh"
 
 namespace bsps {
 
@@ -21,59 +21,31 @@ template <typename K> struct BucketArgs {
 };
 
 template <int DT, bool PAIRS, int CL, int ITEMS>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSortThreads, 1)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(1024, 1)
 bucket_sort_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
-    using CS = ClusterSort<K, PAIRS, kSortThreads, ITEMS, CL>;
-    constexpr int CAP = CS::CAP;
+    using SS = SegSort<K, PAIRS, CL, ITEMS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename CS::Smem &sm = *reinterpret_cast<typename CS::Smem *>(smem_raw);
-    K *kbuf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename CS::Smem) + 15) & ~size_t(15)));
-    uint32_t *vbuf = reinterpret_cast<uint32_t *>(kbuf + CAP);
+    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
+    K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
+    uint32_t *slots = reinterpret_cast<uint32_t *>(buf + SS::CAP);
 
-    auto cluster = cg::this_cluster();
-    const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
     const int64_t v = blockIdx.x / CL;
     const int64_t cnt = imin64(a.vsize[v], a.cap);
     if (cnt == 0) return;
-    if (cnt > (int64_t)CL * CAP) {  // whole cluster leaves together
-        if (rank == 0 && threadIdx.x == 0) {
-            const int slot = atomicAdd(&a.st->slow_buckets, 1);
-            a.slow_list[slot] = (uint32_t)v;
-        }
-        return;
-    }
-    const K *src = a.reg_keys + v * a.cap;
-    K mn = all_ones<K>(), mx = 0;
-    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
-        const int64_t e = (int64_t)rank * CAP + t;
-        K x = all_ones<K>();
-        if (e < cnt) {
-            x = src[e];
-            mn = x < mn ? x : mn;
-            mx = x > mx ? x : mx;
-        }
-        kbuf[t] = x;
-        if constexpr (PAIRS) vbuf[t] = (uint32_t)e;
-    }
-    K base, top;
-    CS::minmax(sm, mn, mx, base, top);
-    const int bits = bit_length<K>(top - base);
-    if (bits > 0) {
-        for (int t = threadIdx.x; t < CAP; t += kSortThreads)
-            if ((int64_t)rank * CAP + t < cnt) kbuf[t] -= base;
-        __syncthreads();
-        CS::sort(sm, kbuf, vbuf, bits);
-    }
     const uint64_t off = a.voff[v];
-    const int k_add = bits > 0;
-    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
-        const int64_t pos = (int64_t)rank * CAP + t;
-        if (pos < cnt) {
-            const K x = k_add ? kbuf[t] + base : kbuf[t];
-            a.out_keys[off + pos] = KeyTraits<DT>::inv(x);
-            if constexpr (PAIRS) a.out_vals[off + pos] = a.reg_vals[v * a.cap + vbuf[t]];
-        }
+    const K *src = a.reg_keys + v * a.cap;
+    const uint32_t *vsrc = a.reg_vals + v * a.cap;
+    K *out_k = a.out_keys + off;
+    uint32_t *out_v = a.out_vals + off;
+    auto emit = [&](uint32_t pos, K key, uint32_t slot) {
+        out_k[pos] = KeyTraits<DT>::inv(key);
+        if constexpr (PAIRS) out_v[pos] = vsrc[slot];
+    };
+    const bool done = SS::run(sm, buf, slots, cnt, [&](int64_t e) { return src[e]; }, emit);
+    if (!done && blockIdx.x % CL == 0 && threadIdx.x == 0) {
+        const int slot = atomicAdd(&a.st->slow_buckets, 1);
+        a.slow_list[slot] = (uint32_t)v;
     }
 }
 
@@ -174,12 +146,12 @@ __global__ void __launch_bounds__(kSlowThreads) bucket_slow_kernel(BucketArgs<ty
 
 template <int DT, bool PAIRS, int CL, int ITEMS> static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
     using K = typename KeyTraits<DT>::T;
-    using CS = ClusterSort<K, PAIRS, kSortThreads, ITEMS, CL>;
-    const size_t smem = ((sizeof(typename CS::Smem) + 15) & ~size_t(15)) + CS::CAP * (sizeof(K) + (PAIRS ? 4 : 0));
+    using SS = SegSort<K, PAIRS, CL, ITEMS>;
+    const size_t smem = SS::smem_bytes();
     auto kern = bucket_sort_kernel<DT, PAIRS, CL, ITEMS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(c.pl.P * CL), kSortThreads, smem, c.stream>>>(a);
+    kern<<<(unsigned)(c.pl.P * CL), 1024, smem, c.stream>>>(a);
     return cudaGetLastError();
 }
 

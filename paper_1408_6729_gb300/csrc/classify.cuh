@@ -13,7 +13,7 @@ namespace bsps {
 // share the key's cell.  The result is exactly the splitter-tree descent.
 template <typename K>
 __device__ __forceinline__ uint32_t classify_key(K phi, uint32_t tag, const LutParams<K> &lp,
-                                                 const uint32_t *lut, const K *sphi,
+                                                 const uint16_t *lut, const K *sphi,
                                                  const uint32_t *stag) {
     if (phi < lp.base) return 0;
     const K d = phi - lp.base;

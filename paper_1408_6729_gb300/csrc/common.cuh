@@ -62,7 +62,8 @@ struct DevStatus {
     unsigned long long mispredicted;
     unsigned long long correction_steps;
     uint32_t tile_counter;      // dynamic tile ticket of the routing kernel
-    uint32_t pad_[7];
+    uint32_t run_too_big;       // a block of the regular sample did not fit on chip
+    uint32_t pad_[6];
 };
 
 __device__ __forceinline__ void set_error(DevStatus *st, int code) {

@@ -6,30 +6,33 @@
 
 namespace bsps {
 
+struct MlpNorm;
+
 // Number of cells of the radix index placed in front of the splitter tree.
-constexpr int kLutBits = 13;
+constexpr int kLutBits = 12;
 constexpr int kLutCells = 1 << kLutBits;
 
 // Routing geometry (Fig. 1 steps 9-11).
-constexpr int kRouteThreads = 512;
-constexpr int kRouteItems = 8;                              // keys per thread per chunk
-constexpr int kRouteChunk = kRouteThreads * kRouteItems;    // keys staged in shared memory
-constexpr int kRouteChunksPerTile = 16;
-constexpr int kRouteTile = kRouteChunk * kRouteChunksPerTile;  // keys per lookback tile
+constexpr int kRouteThreads = 1024;
+constexpr int kRouteTile = 65536;                           // keys per look-back tile
+template <typename K> constexpr int route_items() { return sizeof(K) == 8 ? 4 : 8; }
+template <typename K> constexpr int route_chunk() { return kRouteThreads * route_items<K>(); }
+constexpr size_t kRouteSmemBudget = 220 * 1024;
 
 // Sample-sort geometry (Fig. 1 step 5).
 constexpr int kLsdThreads = 512;
 constexpr int kLsdItems = 16;
 constexpr int kLsdTile = kLsdThreads * kLsdItems;
 
-// Bucket / block sort geometry (Fig. 1 step 3, Fig. 2 step 12).
-constexpr int kSortThreads = 512;
-constexpr int kRunItems32 = 16;        // block sort with input-slot companion, 4-byte keys
-constexpr int kRunItems64 = 12;        // ... 8-byte keys
-constexpr int kBucketItems32 = 32;     // sub-bucket sort, keys only, 4-byte keys
-constexpr int kBucketItems64 = 16;     // ... 8-byte keys
-constexpr int kPairItems32 = 16;       // sub-bucket sort with payload slots, 4-byte keys
-constexpr int kPairItems64 = 12;       // ... 8-byte keys
+// Bucket / block sort geometry (Fig. 1 step 3, Fig. 2 step 12): 1024-thread
+// CTAs, keys per thread of the on-chip segment sort.
+constexpr int kSortThreads = 1024;
+constexpr int kRunItems32 = 10;        // block sort with input-slot companion, 4-byte keys
+constexpr int kRunItems64 = 8;         // ... 8-byte keys
+constexpr int kBucketItems32 = 14;     // sub-bucket sort, keys only, 4-byte keys
+constexpr int kBucketItems64 = 10;     // ... 8-byte keys
+constexpr int kPairItems32 = 12;       // sub-bucket sort with payload slots, 4-byte keys
+constexpr int kPairItems64 = 8;        // ... 8-byte keys
 constexpr int kSlowThreads = 512;      // out-of-core sort of an oversized sub-bucket
 constexpr int kSlowItems = 8;
 
@@ -73,9 +76,17 @@ struct Layout {
     int32_t *lsd_table;     // pass table of the sample sort
     void *vphi;             // P-1 sub-bucket splitters, phi
     uint32_t *vtag;         // P-1 sub-bucket splitters, tag
-    uint32_t *lut;          // kLutCells + 1
+    uint16_t *lut;          // kLutCells + 1 (sub-bucket counts fit 16 bits)
     void *lutp;             // LutParams<K>
     uint32_t *state;        // tiles * P lookback words
+    uint16_t *ids;          // tiles * kRouteTile sub-bucket ids (routing scratch)
+    uint32_t *cursor;       // P keys routed per sub-bucket
+    // learned classifier (classify == BSPS_LEARNED)
+    float *mlp_params, *mlp_m, *mlp_v;   // 1153 each
+    float *mlp_part;                     // training grid x 1154 partial sums
+    float *mlp_x, *mlp_y;                // training points
+    int64_t *mlp_npts;
+    struct MlpNorm *mlp_norm;
     void *reg_keys;         // P * cap keys (phi), region v at v*cap
     uint32_t *reg_vals;     // P * cap payloads
     uint32_t *vsize;        // P sub-bucket sizes
@@ -106,6 +117,7 @@ cudaError_t launch_splitters(const Ctx &c);       // Fig. 1 steps 6-7
 cudaError_t launch_route(const Ctx &c);           // Fig. 1 steps 9-11
 cudaError_t launch_bucket_sort(const Ctx &c);     // Fig. 2 step 12
 cudaError_t launch_debug(const Ctx &c);           // optional diagnostics
+cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, init, Adam
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);

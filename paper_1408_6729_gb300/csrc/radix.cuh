@@ -21,6 +21,20 @@ __device__ __forceinline__ int striped_slot(int i) {
     return warp * 32 * ITEMS + i * 32 + lane;
 }
 
+// Lanes of the warp holding the same digit, from one ballot per digit bit
+// (cheaper than a match instruction when most digits differ).
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
 // Stable ranking of ITEMS digits per thread (RADIX_BITS-bit digits).
 // After rank(): rank[i] = number of items with the same digit and a smaller
 // slot; digit_tot[d] = number of items with digit d in this CTA.
@@ -42,7 +56,7 @@ struct BlockRank {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t d = digit[i];
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t peers = warp_peers<RADIX_BITS>(d);
             const uint32_t before = __popc(peers & lt);
             const uint32_t cnt = sm.warp_hist[warp][d];
             __syncwarp();
@@ -65,7 +79,50 @@ struct BlockRank {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) rk[i] += sm.warp_hist[warp][digit[i]];
     }
+
+    // As rank(), for the first `ia` items of every thread only (ia is the same
+    // for the whole CTA; the slot of item i is warp*32*ia + i*32 + lane).
+    __device__ static void rank_n(Smem &sm, const uint32_t (&digit)[ITEMS], uint32_t (&rk)[ITEMS], int ia) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int d = lane; d < RADIX; d += 32) sm.warp_hist[warp][d] = 0;
+        __syncwarp();
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            if (i < ia) {
+                const uint32_t d = digit[i];
+                const uint32_t peers = warp_peers<RADIX_BITS>(d);
+                const uint32_t before = __popc(peers & lt);
+                const uint32_t cnt = sm.warp_hist[warp][d];
+                __syncwarp();
+                if (before == 0) sm.warp_hist[warp][d] = (uint16_t)(cnt + __popc(peers));
+                __syncwarp();
+                rk[i] = cnt + before;
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < RADIX; d += THREADS) {
+            uint32_t run = 0;
+#pragma unroll 8
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t c = sm.warp_hist[w][d];
+                sm.warp_hist[w][d] = (uint16_t)run;
+                run += c;
+            }
+            sm.digit_tot[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (i < ia) rk[i] += sm.warp_hist[warp][digit[i]];
+    }
 };
+
+template <int THREADS>
+__device__ __forceinline__ int striped_slot_n(int i, int ia) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    return warp * 32 * ia + i * 32 + lane;
+}
 
 // Exclusive scan of RADIX (<= THREADS) values held in `v[]` (in place).
 template <int THREADS, int RADIX>

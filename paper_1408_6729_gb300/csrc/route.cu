@@ -12,6 +12,7 @@
 // region.  Keys keep input order inside every region (Fig. 1 step 11: "the
 // initial ordering of the keys is preserved").
 #include "classify.cuh"
+#include "mlp.cuh"
 #include "radix.cuh"
 
 namespace bsps {
@@ -25,20 +26,24 @@ template <typename K> struct RouteArgs {
     const uint32_t *vals;
     int64_t n;
     const LutParams<K> *lutp;
-    const uint32_t *lut;
+    const uint16_t *lut;
     const K *vphi;
     const uint32_t *vtag;
     uint32_t P;
     int64_t tiles;
     uint32_t *state;
+    uint32_t *cursor;   // keys routed so far per sub-bucket
+    uint16_t *ids;      // sub-bucket of every key, written by phase A, read by phase B
     K *reg_keys;
     uint32_t *reg_vals;
     int64_t cap;
     DevStatus *st;
+    const float *mlp_params;     // learned classifier (nullable)
+    const MlpNorm *mlp_norm;
 };
 
 template <typename K> struct RouteFixed {
-    typename BlockRank<kRouteThreads, kRouteItems, 8>::Smem rank;
+    typename BlockRank<kRouteThreads, route_items<K>(), 8>::Smem rank;
     uint32_t base[256];
     uint32_t tmp[40];
     uint32_t warp_max[kRouteThreads / 32];
@@ -46,49 +51,73 @@ template <typename K> struct RouteFixed {
     LutParams<K> lp;
 };
 
-template <typename K, bool PAIRS> struct RouteSmemLayout {
-    size_t lut, sphi, stag, run, stage_k, stage_v, stage_b, total;
+// Shared memory of the routing kernel.  The splitters' phi live in shared
+// memory when they fit next to the rest, in global memory (L1-cached)
+// otherwise; their tags, read only on ties, stay in global memory.
+template <typename K, bool PAIRS, bool LEARNED = false> struct RouteSmemLayout {
+    size_t mlp, lut, sphi, run, coff, stage_k, stage_v, stage_b, total;
+    bool sphi_in_smem;
     __host__ __device__ RouteSmemLayout(uint32_t P) {
-        size_t o = (sizeof(RouteFixed<K>) + 15) & ~size_t(15);
-        lut = o;     o += sizeof(uint32_t) * (kLutCells + 1);
-        o = (o + 15) & ~size_t(15);
-        sphi = o;    o += sizeof(K) * (P > 1 ? P - 1 : 1);
-        o = (o + 15) & ~size_t(15);
-        stag = o;    o += sizeof(uint32_t) * (P > 1 ? P - 1 : 1);
-        o = (o + 15) & ~size_t(15);
-        run = o;     o += sizeof(uint32_t) * P;
-        o = (o + 15) & ~size_t(15);
-        stage_k = o; o += sizeof(K) * kRouteChunk;
-        stage_v = o; o += PAIRS ? sizeof(uint32_t) * kRouteChunk : 0;
-        stage_b = o; o += sizeof(uint32_t) * kRouteChunk;
-        total = o;
+        for (int pass = 0; pass < 2; ++pass) {
+            sphi_in_smem = pass == 0;
+            size_t o = (sizeof(RouteFixed<K>) + 15) & ~size_t(15);
+            mlp = o;     o += LEARNED ? sizeof(float) * (kParams + 3) + sizeof(MlpNorm) : 0;
+            o = (o + 15) & ~size_t(15);
+            lut = o;     o += sizeof(uint16_t) * (kLutCells + 1);
+            o = (o + 15) & ~size_t(15);
+            sphi = o;    o += sphi_in_smem ? sizeof(K) * (P > 1 ? P - 1 : 1) : 0;
+            o = (o + 15) & ~size_t(15);
+            run = o;     o += sizeof(uint32_t) * P;
+            coff = o;    o += PAIRS ? 0 : sizeof(uint32_t) * (P + 1);
+            o = (o + 15) & ~size_t(15);
+            stage_k = o; o += sizeof(K) * route_chunk<K>();
+            stage_v = o; o += PAIRS ? sizeof(uint32_t) * route_chunk<K>() : 0;
+            stage_b = o; o += sizeof(uint16_t) * route_chunk<K>();
+            total = o;
+            if (total <= kRouteSmemBudget) break;
+        }
     }
 };
 
-template <int DT, bool PAIRS>
+__device__ __forceinline__ void discard_l2_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
+template <int DT, bool PAIRS, bool LEARNED>
 __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
-    using Rank = BlockRank<kRouteThreads, kRouteItems, 8>;
-    constexpr int IT = kRouteItems;
+    constexpr int IT = route_items<K>();
+    constexpr int TH = kRouteThreads;
+    constexpr int CH = route_chunk<K>();
+    using Rank = BlockRank<TH, IT, 8>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RouteSmemLayout<K, PAIRS> L(a.P);
+    const RouteSmemLayout<K, PAIRS, LEARNED> L(a.P);
+    float *mw = reinterpret_cast<float *>(smem_raw + L.mlp);
+    MlpNorm *mnorm = reinterpret_cast<MlpNorm *>(mw + kParams + 3);
+    uint32_t n_mis = 0, n_steps = 0;
     RouteFixed<K> &fx = *reinterpret_cast<RouteFixed<K> *>(smem_raw);
-    uint32_t *lut = reinterpret_cast<uint32_t *>(smem_raw + L.lut);
-    K *sphi = reinterpret_cast<K *>(smem_raw + L.sphi);
-    uint32_t *stag = reinterpret_cast<uint32_t *>(smem_raw + L.stag);
+    uint16_t *lut = reinterpret_cast<uint16_t *>(smem_raw + L.lut);
+    K *sphi_s = reinterpret_cast<K *>(smem_raw + L.sphi);
+    const K *sphi = L.sphi_in_smem ? sphi_s : a.vphi;
+    const uint32_t *stag = a.vtag;
     uint32_t *run = reinterpret_cast<uint32_t *>(smem_raw + L.run);
+    uint32_t *coff = reinterpret_cast<uint32_t *>(smem_raw + L.coff);
     K *stage_k = reinterpret_cast<K *>(smem_raw + L.stage_k);
     uint32_t *stage_v = reinterpret_cast<uint32_t *>(smem_raw + L.stage_v);
-    uint32_t *stage_b = reinterpret_cast<uint32_t *>(smem_raw + L.stage_b);
+    uint16_t *stage_b = reinterpret_cast<uint16_t *>(smem_raw + L.stage_b);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t P = a.P, nsplit = P - 1;
 
     // splitters and radix index into shared memory (Fig. 1 step 7, "broadcast")
-    for (int i = tid; i <= kLutCells; i += kRouteThreads) lut[i] = a.lut[i];
-    for (uint32_t i = tid; i < nsplit; i += kRouteThreads) {
-        sphi[i] = a.vphi[i];
-        stag[i] = a.vtag[i];
+    for (int i = tid; i <= kLutCells; i += TH) lut[i] = a.lut[i];
+    if (L.sphi_in_smem)
+        for (uint32_t i = tid; i < nsplit; i += TH) sphi_s[i] = a.vphi[i];
+    if constexpr (!PAIRS)
+        for (uint32_t b = tid; b <= P; b += TH) coff[b] = 0;
+    if constexpr (LEARNED) {
+        for (int k = tid; k < kParams; k += TH) mw[k] = a.mlp_params[k];
+        if (tid == 0) *mnorm = *a.mlp_norm;
     }
     if (tid == 0) fx.lp = *a.lutp;
     __syncthreads();
@@ -102,164 +131,262 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
         if (tile >= a.tiles) break;
         const int64_t t0 = tile * kRouteTile;
         const int64_t tlen = imin64(kRouteTile, a.n - t0);
+        uint16_t *ids = a.ids + t0;
 
-        // ---- counts per sub-bucket of this tile (Fig. 1 step 9) ----
-        for (uint32_t b = tid; b < P; b += kRouteThreads) run[b] = 0;
+        // ---- classify and count per sub-bucket (Fig. 1 step 9) ----
+        for (uint32_t b = tid; b < P; b += TH) run[b] = 0;
         __syncthreads();
-        for (int64_t cs = 0; cs < tlen; cs += kRouteChunk) {
+        for (int64_t cs = 0; cs < tlen; cs += CH) {
             K kk[IT];
-            bool ok[IT];
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
-                const int64_t e = cs + striped_slot<kRouteThreads, IT>(i);
-                ok[i] = e < tlen;
-                kk[i] = ok[i] ? a.keys[t0 + e] : K(0);
+                const int64_t e = cs + i * TH + tid;
+                kk[i] = e < tlen ? a.keys[t0 + e] : K(0);
             }
 #pragma unroll
             for (int i = 0; i < IT; ++i) {
-                const int64_t e = cs + striped_slot<kRouteThreads, IT>(i);
-                const uint32_t b = ok[i] ? classify_key(KeyTraits<DT>::phi(kk[i]), (uint32_t)(t0 + e), lp,
-                                                        lut, sphi, stag)
-                                         : 0xffffffffu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, b);
-                if (ok[i] && (peers & lanemask_lt()) == 0) atomicAdd(&run[b], (uint32_t)__popc(peers));
+                const int64_t e = cs + i * TH + tid;
+                const bool ok = e < tlen;
+                uint32_t b = 0xffffffffu;
+                if constexpr (LEARNED) {
+                    if (ok) {
+                        uint32_t steps;
+                        b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), mw, *mnorm, P, sphi, stag, steps);
+                        n_mis += steps > 0;
+                        n_steps += steps;
+                    }
+                } else {
+                    if (ok) b = classify_key(KeyTraits<DT>::phi(kk[i]), (uint32_t)(t0 + e), lp, lut, sphi, stag);
+                }
+                // keys of lane 0's bucket are counted with one atomic (runs
+                // of equal buckets are common in skewed inputs)
+                const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+                const uint32_t same = __ballot_sync(0xffffffffu, ok && b == b0);
+                if (ok) {
+                    if (b != b0) atomicAdd(&run[b], 1u);
+                    else if (lane == __ffs(same) - 1) atomicAdd(&run[b], (uint32_t)__popc(same));
+                    ids[e] = (uint16_t)b;
+                }
             }
         }
         __syncthreads();
 
-        // ---- publish, look back, publish the inclusive prefix (Lemma 4.2) ----
-        uint32_t *my = a.state + tile * P;
-        if (tile == 0) {
-            for (uint32_t b = tid; b < P; b += kRouteThreads) {
-                const uint32_t cnt = run[b];
-                st_volatile(&my[b], kFlagP | cnt);
-                run[b] = 0;
-                if (cnt > a.cap) { atomicExch(&a.st->overflow, 1); set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW); }
-            }
-        } else {
-            for (uint32_t b = tid; b < P; b += kRouteThreads) st_volatile(&my[b], kFlagA | run[b]);
-            for (uint32_t b = tid; b < P; b += kRouteThreads) {
-                uint32_t excl = 0;
-                for (int64_t t = tile - 1; t >= 0; --t) {
-                    const uint32_t *w = a.state + t * P + b;
-                    uint32_t v = ld_volatile(w), polls = 0;
-                    while ((v >> 30) == 0 && ++polls < kSpinLimit) {
-                        // after any expired wait, nobody waits any more
-                        if ((polls & 255) == 0 && ld_volatile((const uint32_t *)&a.st->timeouts) != 0) break;
-                        __nanosleep(64);
-                        v = ld_volatile(w);
-                    }
-                    if ((v >> 30) == 0) {
-                        atomicAdd(&a.st->timeouts, 1);
-                        set_error(a.st, BSPS_ERR_DEVICE_TIMEOUT);
-                        break;
-                    }
-                    excl += v & kValMask;
-                    if ((v >> 30) == 2) break;
-                }
-                const uint32_t cnt = run[b];
-                st_volatile(&my[b], kFlagP | ((excl + cnt) & kValMask));
-                run[b] = excl;
-                if ((uint64_t)excl + cnt > (uint64_t)a.cap) {
+        // ---- where this tile's keys go inside every sub-bucket region ----
+        if constexpr (!PAIRS) {
+            // keys only: the order of equal-bucket keys inside a region is
+            // free, so each tile reserves its runs with one atomic per bucket
+            for (uint32_t b = tid; b < P; b += TH) {
+                const uint32_t c = run[b];
+                const uint32_t at = c ? atomicAdd(&a.cursor[b], c) : 0u;
+                run[b] = at;
+                if ((uint64_t)at + c > (uint64_t)a.cap) {
                     atomicExch(&a.st->overflow, 1);
                     set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
                 }
             }
+        } else {
+            // with payloads: input order is kept (Fig. 1 step 11), so every
+            // tile needs the keys of each bucket in all earlier tiles -- the
+            // p parallel prefix sums of Fig. 1 step 9 (Lemma 4.2), done as a
+            // decoupled look-back over earlier tiles' published counts
+            uint32_t *my = a.state + tile * P;
+            for (uint32_t b = tid; b < P; b += TH) {
+                st_volatile(&my[b], (tile == 0 ? kFlagP : kFlagA) | run[b]);
+                if (run[b]) atomicAdd(&a.cursor[b], run[b]);
+            }
+            if (tile > 0) {
+                for (uint32_t b = tid; b < P; b += TH) {
+                    uint32_t excl = 0;
+                    bool done = false;
+                    for (int64_t t = tile - 1; t >= 0 && !done; t -= 8) {
+                        uint32_t v[8];
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) v[w] = t - w >= 0 ? ld_volatile(a.state + (t - w) * P + b) : kFlagP;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            if (done) break;
+                            uint32_t x = v[w], polls = 0;
+                            while ((x >> 30) == 0 && ++polls < kSpinLimit) {
+                                // after any expired wait, nobody waits any more
+                                if ((polls & 255) == 0 && ld_volatile((const uint32_t *)&a.st->timeouts) != 0) break;
+                                __nanosleep(64);
+                                x = ld_volatile(a.state + (t - w) * P + b);
+                            }
+                            if ((x >> 30) == 0) {
+                                atomicAdd(&a.st->timeouts, 1);
+                                set_error(a.st, BSPS_ERR_DEVICE_TIMEOUT);
+                                done = true;
+                                break;
+                            }
+                            excl += x & kValMask;
+                            done = (x >> 30) == 2;
+                        }
+                    }
+                    const uint32_t c = run[b];
+                    st_volatile(&my[b], kFlagP | ((excl + c) & kValMask));
+                    run[b] = excl;
+                    if ((uint64_t)excl + c > (uint64_t)a.cap) {
+                        atomicExch(&a.st->overflow, 1);
+                        set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
+                    }
+                }
+            } else {
+                for (uint32_t b = tid; b < P; b += TH) {
+                    if (run[b] > a.cap) {
+                        atomicExch(&a.st->overflow, 1);
+                        set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
+                    }
+                    run[b] = 0;
+                }
+            }
         }
         __syncthreads();
 
-        // ---- route: stable partition of each chunk by sub-bucket, then one
-        //      contiguous write per sub-bucket run (Fig. 1 step 11) ----
-        for (int64_t cs = 0; cs < tlen; cs += kRouteChunk) {
-            const int clen = (int)imin64(kRouteChunk, tlen - cs);
-            K kk[IT];
-            uint32_t vv[IT], bb[IT], d[IT], rk[IT];
-#pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int s = striped_slot<kRouteThreads, IT>(i);
-                if (s < clen) {
-                    kk[i] = KeyTraits<DT>::phi(a.keys[t0 + cs + s]);
-                    if constexpr (PAIRS) vv[i] = a.vals[t0 + cs + s];
-                } else {
-                    kk[i] = 0;
-                    if constexpr (PAIRS) vv[i] = 0;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int s = striped_slot<kRouteThreads, IT>(i);
-                bb[i] = s < clen ? classify_key(kk[i], (uint32_t)(t0 + cs + s), lp, lut, sphi, stag) : P;
-            }
-            for (int shift = 0; shift < bbits; shift += 8) {
-#pragma unroll
-                for (int i = 0; i < IT; ++i) d[i] = (bb[i] >> shift) & 255u;
-                Rank::rank(fx.rank, d, rk);
-                for (int dd = tid; dd < 256; dd += kRouteThreads) fx.base[dd] = fx.rank.digit_tot[dd];
-                __syncthreads();
-                digit_excl_scan<kRouteThreads, 256>(fx.base, fx.tmp);
+        // ---- route (Fig. 1 step 11): each chunk is grouped by sub-bucket in
+        //      shared memory and every sub-bucket run is written contiguously ----
+        for (int64_t cs = 0; cs < tlen; cs += CH) {
+            const int clen = (int)imin64(CH, tlen - cs);
+            if constexpr (!PAIRS) {
+                // keys only: order inside a run is free, ranks come from atomics
+                K kk[IT];
+                uint32_t bb[IT], rk[IT];
 #pragma unroll
                 for (int i = 0; i < IT; ++i) {
-                    const uint32_t pos = fx.base[d[i]] + rk[i];
-                    stage_k[pos] = kk[i];
-                    if constexpr (PAIRS) stage_v[pos] = vv[i];
-                    stage_b[pos] = bb[i];
+                    const int s = i * TH + tid;
+                    const bool ok = s < clen;
+                    kk[i] = ok ? KeyTraits<DT>::phi(a.keys[t0 + cs + s]) : K(0);
+                    bb[i] = ok ? (uint32_t)ids[cs + s] : P;
+                }
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const uint32_t b = bb[i];
+                    const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+                    const uint32_t same = __ballot_sync(0xffffffffu, b == b0);
+                    if (b == b0) {
+                        const int leader = __ffs(same) - 1;
+                        uint32_t r0 = 0;
+                        if (lane == leader) r0 = atomicAdd(&coff[b], (uint32_t)__popc(same));
+                        r0 = __shfl_sync(same, r0, leader);
+                        rk[i] = r0 + __popc(same & lanemask_lt());
+                    } else {
+                        rk[i] = atomicAdd(&coff[b], 1u);
+                    }
                 }
                 __syncthreads();
-                if (shift + 8 < bbits) {
+                block_excl_scan_smem<TH>(coff, (int)P + 1, fx.tmp);
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const uint32_t pos = coff[bb[i]] + rk[i];
+                    stage_k[pos] = kk[i];
+                    stage_b[pos] = (uint16_t)bb[i];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const int s = i * TH + tid;
+                    const uint32_t b = stage_b[s];
+                    if (b < P) {
+                        const uint32_t idx = run[b] + (uint32_t)s - coff[b];
+                        if (idx < a.cap) a.reg_keys[(int64_t)b * a.cap + idx] = stage_k[s];
+                    }
+                }
+                __syncthreads();
+                for (uint32_t b = tid; b < P; b += TH) run[b] += coff[b + 1] - coff[b];
+                __syncthreads();
+                for (uint32_t b = tid; b <= P; b += TH) coff[b] = 0;
+                __syncthreads();
+            } else {
+                // with payloads: stable partition by sub-bucket (LSD over its bits)
+                K kk[IT];
+                uint32_t vv[IT], bb[IT], d[IT], rk[IT];
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const int s = striped_slot<TH, IT>(i);
+                    const bool ok = s < clen;
+                    kk[i] = ok ? KeyTraits<DT>::phi(a.keys[t0 + cs + s]) : K(0);
+                    vv[i] = ok ? a.vals[t0 + cs + s] : 0u;
+                    bb[i] = ok ? (uint32_t)ids[cs + s] : P;
+                }
+                for (int shift = 0; shift < bbits; shift += 8) {
+#pragma unroll
+                    for (int i = 0; i < IT; ++i) d[i] = (bb[i] >> shift) & 255u;
+                    Rank::rank(fx.rank, d, rk);
+                    for (int dd = tid; dd < 256; dd += TH) fx.base[dd] = fx.rank.digit_tot[dd];
+                    __syncthreads();
+                    digit_excl_scan<TH, 256>(fx.base, fx.tmp);
 #pragma unroll
                     for (int i = 0; i < IT; ++i) {
-                        const int s = striped_slot<kRouteThreads, IT>(i);
-                        kk[i] = stage_k[s];
-                        if constexpr (PAIRS) vv[i] = stage_v[s];
-                        bb[i] = stage_b[s];
+                        const uint32_t pos = fx.base[d[i]] + rk[i];
+                        stage_k[pos] = kk[i];
+                        stage_v[pos] = vv[i];
+                        stage_b[pos] = (uint16_t)bb[i];
                     }
                     __syncthreads();
-                }
-            }
-            // staged keys are ordered by sub-bucket; find each run's first slot
-            uint32_t seg[IT];
-            uint32_t carry = 0;
+                    if (shift + 8 < bbits) {
 #pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int s = striped_slot<kRouteThreads, IT>(i);
-                const uint32_t b = stage_b[s];
-                const bool head = s == 0 || stage_b[s - 1] != b;
-                uint32_t x = head ? (uint32_t)s : 0u;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x = max(x, y);
-                }
-                x = max(x, carry);
-                seg[i] = x;
-                carry = __shfl_sync(0xffffffffu, x, 31);
-            }
-            if (lane == 0) fx.warp_max[warp] = carry;
-            __syncthreads();
-            uint32_t pre = 0;
-            for (int w = 0; w < warp; ++w) pre = max(pre, fx.warp_max[w]);
-#pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int s = striped_slot<kRouteThreads, IT>(i);
-                const uint32_t b = stage_b[s];
-                seg[i] = max(seg[i], pre);
-                if (b < P) {
-                    const uint32_t idx = run[b] + (uint32_t)s - seg[i];
-                    if (idx < a.cap) {
-                        a.reg_keys[(int64_t)b * a.cap + idx] = stage_k[s];
-                        if constexpr (PAIRS) a.reg_vals[(int64_t)b * a.cap + idx] = stage_v[s];
+                        for (int i = 0; i < IT; ++i) {
+                            const int s = striped_slot<TH, IT>(i);
+                            kk[i] = stage_k[s];
+                            vv[i] = stage_v[s];
+                            bb[i] = stage_b[s];
+                        }
+                        __syncthreads();
                     }
                 }
-            }
-            __syncthreads();
+                // staged keys are ordered by sub-bucket; find each run's first slot
+                uint32_t seg[IT];
+                uint32_t carry = 0;
 #pragma unroll
-            for (int i = 0; i < IT; ++i) {
-                const int s = striped_slot<kRouteThreads, IT>(i);
-                const uint32_t b = stage_b[s];
-                const bool tail = s == kRouteChunk - 1 || stage_b[s + 1] != b;
-                if (b < P && tail) run[b] += (uint32_t)s - seg[i] + 1;
+                for (int i = 0; i < IT; ++i) {
+                    const int s = striped_slot<TH, IT>(i);
+                    const uint32_t b = stage_b[s];
+                    const bool head = s == 0 || stage_b[s - 1] != b;
+                    uint32_t x = head ? (uint32_t)s : 0u;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x = max(x, y);
+                    }
+                    x = max(x, carry);
+                    seg[i] = x;
+                    carry = __shfl_sync(0xffffffffu, x, 31);
+                }
+                if (lane == 0) fx.warp_max[warp] = carry;
+                __syncthreads();
+                uint32_t pre = 0;
+                for (int w = 0; w < warp; ++w) pre = max(pre, fx.warp_max[w]);
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const int s = striped_slot<TH, IT>(i);
+                    const uint32_t b = stage_b[s];
+                    seg[i] = max(seg[i], pre);
+                    if (b < P) {
+                        const uint32_t idx = run[b] + (uint32_t)s - seg[i];
+                        if (idx < a.cap) {
+                            a.reg_keys[(int64_t)b * a.cap + idx] = stage_k[s];
+                            a.reg_vals[(int64_t)b * a.cap + idx] = stage_v[s];
+                        }
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < IT; ++i) {
+                    const int s = striped_slot<TH, IT>(i);
+                    const uint32_t b = stage_b[s];
+                    const bool tail = s == CH - 1 || stage_b[s + 1] != b;
+                    if (b < P && tail) run[b] += (uint32_t)s - seg[i] + 1;
+                }
+                __syncthreads();
             }
-            __syncthreads();
+        }
+        // the sub-bucket ids of this tile are dead: drop them from L2 unwritten
+        for (int64_t line = tid; line * 64 < tlen; line += TH) discard_l2_line(ids + line * 64);
+    }
+    if constexpr (LEARNED) {  // misprediction statistics of the learned classifier
+        const uint32_t m = __reduce_add_sync(0xffffffffu, n_mis), st = __reduce_add_sync(0xffffffffu, n_steps);
+        if (lane == 0 && (m | st)) {
+            atomicAdd(&a.st->mispredicted, (unsigned long long)m);
+            atomicAdd(&a.st->correction_steps, (unsigned long long)st);
         }
     }
 }
@@ -269,17 +396,16 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
 // bucket sizes for the caller and the balance statistics (Lemma 5.1).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
-bucket_finish_kernel(const uint32_t *state, int64_t tiles, uint32_t P, int64_t B, int64_t cap,
-                     uint32_t *vsize, uint64_t *voff, int64_t *bucket_sizes, DevStatus *st) {
+bucket_finish_kernel(const uint32_t *cursor, uint32_t P, int64_t B, int64_t cap, uint32_t *vsize, uint64_t *voff,
+                     int64_t *bucket_sizes, DevStatus *st) {
     __shared__ uint32_t tmp[40];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t *last = state + (tiles - 1) * (int64_t)P;
     const int64_t per = ((int64_t)P + 1023) / 1024;
     const int64_t lo = tid * per, hi = imin64(P, lo + per);
     uint64_t local = 0;
     uint32_t vmax = 0;
     for (int64_t v = lo; v < hi; ++v) {
-        const uint32_t s = last[v] & kValMask;
+        const uint32_t s = cursor[v];
         vsize[v] = s;
         local += s;
         vmax = max(vmax, s);
@@ -315,7 +441,7 @@ bucket_finish_kernel(const uint32_t *state, int64_t tiles, uint32_t P, int64_t B
     }
 }
 
-template <int DT, bool PAIRS> static cudaError_t launch_route_t(const Ctx &c) {
+template <int DT, bool PAIRS, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) {
     using K = typename KeyTraits<DT>::T;
     const Plan &p = c.pl;
     RouteArgs<K> a;
@@ -329,12 +455,16 @@ template <int DT, bool PAIRS> static cudaError_t launch_route_t(const Ctx &c) {
     a.P = (uint32_t)p.P;
     a.tiles = p.tiles;
     a.state = c.ly.state;
+    a.cursor = c.ly.cursor;
+    a.ids = c.ly.ids;
     a.reg_keys = (K *)c.ly.reg_keys;
     a.reg_vals = c.ly.reg_vals;
     a.cap = p.cap;
     a.st = c.ly.status;
-    const size_t smem = RouteSmemLayout<K, PAIRS>((uint32_t)p.P).total;
-    auto kern = route_kernel<DT, PAIRS>;
+    a.mlp_params = c.ly.mlp_params;
+    a.mlp_norm = c.ly.mlp_norm;
+    const size_t smem = RouteSmemLayout<K, PAIRS, LEARNED>((uint32_t)p.P).total;
+    auto kern = route_kernel<DT, PAIRS, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -345,25 +475,34 @@ template <int DT, bool PAIRS> static cudaError_t launch_route_t(const Ctx &c) {
     kern<<<(unsigned)grid, kRouteThreads, smem, c.stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bucket_finish_kernel<<<1, 1024, 0, c.stream>>>(c.ly.state, p.tiles, (uint32_t)p.P, p.B, p.cap, c.ly.vsize,
-                                                   c.ly.voff, c.bucket_sizes, c.ly.status);
+    bucket_finish_kernel<<<1, 1024, 0, c.stream>>>(c.ly.cursor, (uint32_t)p.P, p.B, p.cap, c.ly.vsize, c.ly.voff,
+                                                   c.bucket_sizes, c.ly.status);
     return cudaGetLastError();
 }
 
+template <int DT> static cudaError_t launch_route_d(const Ctx &c) {
+    const bool pr = c.pl.pairs != 0, learned = c.pl.classify == BSPS_LEARNED;
+    if (learned) return pr ? launch_route_t<DT, true, true>(c) : launch_route_t<DT, false, true>(c);
+    return pr ? launch_route_t<DT, true, false>(c) : launch_route_t<DT, false, false>(c);
+}
+
 cudaError_t launch_route(const Ctx &c) {
-    const bool pr = c.pl.pairs != 0;
     switch (c.pl.dtype) {
-    case BSPS_U32: return pr ? launch_route_t<BSPS_U32, true>(c) : launch_route_t<BSPS_U32, false>(c);
-    case BSPS_I32: return pr ? launch_route_t<BSPS_I32, true>(c) : launch_route_t<BSPS_I32, false>(c);
-    case BSPS_F32: return pr ? launch_route_t<BSPS_F32, true>(c) : launch_route_t<BSPS_F32, false>(c);
-    default: return pr ? launch_route_t<BSPS_F64, true>(c) : launch_route_t<BSPS_F64, false>(c);
+    case BSPS_U32: return launch_route_d<BSPS_U32>(c);
+    case BSPS_I32: return launch_route_d<BSPS_I32>(c);
+    case BSPS_F32: return launch_route_d<BSPS_F32>(c);
+    default: return launch_route_d<BSPS_F64>(c);
     }
 }
 
 size_t route_smem_bytes(const Plan &pl) {
     const uint32_t P = (uint32_t)pl.P;
-    if (pl.key_bytes == 8)
+    const bool l = pl.classify == BSPS_LEARNED;
+    if (pl.key_bytes == 8) {
+        if (l) return pl.pairs ? RouteSmemLayout<uint64_t, true, true>(P).total : RouteSmemLayout<uint64_t, false, true>(P).total;
         return pl.pairs ? RouteSmemLayout<uint64_t, true>(P).total : RouteSmemLayout<uint64_t, false>(P).total;
+    }
+    if (l) return pl.pairs ? RouteSmemLayout<uint32_t, true, true>(P).total : RouteSmemLayout<uint32_t, false, true>(P).total;
     return pl.pairs ? RouteSmemLayout<uint32_t, true>(P).total : RouteSmemLayout<uint32_t, false>(P).total;
 }
 

@@ -1,7 +1,7 @@
 // sample.cu -- oversampling, sample sort, splitter selection (Fig. 1 steps
 // 3-7, Fig. 3 steps 3-9) and the optional diagnostics.
 #include "classify.cuh"
-#include "radix.cuh"
+#include "segsort.cuh"
 
 namespace bsps {
 
@@ -38,56 +38,38 @@ __global__ void sample_random_kernel(const typename KeyTraits<DT>::T *__restrict
 template <int DT, int CL, int ITEMS>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSortThreads, 1)
 run_sample_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m,
-                  int64_t M, int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag) {
+                  int64_t M, int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag,
+                  uint32_t *too_big) {
     using K = typename KeyTraits<DT>::T;
-    using CS = ClusterSort<K, true, kSortThreads, ITEMS, CL>;
-    constexpr int CAP = CS::CAP;
+    using SS = SegSort<K, true, CL, ITEMS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename CS::Smem &sm = *reinterpret_cast<typename CS::Smem *>(smem_raw);
-    K *kbuf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename CS::Smem) + 15) & ~size_t(15)));
-    uint32_t *vbuf = reinterpret_cast<uint32_t *>(kbuf + CAP);
+    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
+    K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
+    uint32_t *slots = reinterpret_cast<uint32_t *>(buf + SS::CAP);
 
-    auto cluster = cg::this_cluster();
-    const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
     const int64_t k = blockIdx.x / CL;
     const int64_t lo = k * m;
-    const int64_t len = lo < n ? min(m, n - lo) : 0;
-
-    K mn = all_ones<K>(), mx = 0;
-    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
-        const int64_t e = (int64_t)rank * CAP + t;
-        K v = all_ones<K>();
-        if (e < len) {
-            v = KeyTraits<DT>::phi(keys[lo + e]);
-            mn = v < mn ? v : mn;
-            mx = v > mx ? v : mx;
-        }
-        kbuf[t] = v;
-        vbuf[t] = (uint32_t)e;
-    }
-    K base, top;
-    CS::minmax(sm, mn, mx, base, top);
-    const int bits = len > 0 ? bit_length<K>(top - base) : 0;
-    for (int t = threadIdx.x; t < CAP; t += kSortThreads) {
-        const int64_t e = (int64_t)rank * CAP + t;
-        if (e < len) kbuf[t] -= base;
-    }
-    __syncthreads();
-    CS::sort(sm, kbuf, vbuf, bits);
-    for (int64_t j = 1 + threadIdx.x; j <= s; j += kSortThreads) {
-        const int64_t pos = j * x - 1;
-        const int64_t out = k * s + (j - 1);
-        if (pos >= len) {
-            if (rank == 0) {
-                sphi[out] = all_ones<K>();
-                stag[out] = (uint32_t)(n + k * M + pos);
+    const int64_t len = lo < n ? imin64(m, n - lo) : 0;
+    if (blockIdx.x % CL == 0) {  // pads: sorted positions len..M-1, in tag order
+        for (int64_t j = 1 + threadIdx.x; j <= s; j += kSortThreads) {
+            const int64_t pos = j * x - 1;
+            if (pos >= len) {
+                sphi[k * s + (j - 1)] = all_ones<K>();
+                stag[k * s + (j - 1)] = (uint32_t)(n + k * M + pos);
             }
-        } else if (pos / CAP == rank) {
-            const int slot = (int)(pos % CAP);
-            sphi[out] = kbuf[slot] + base;
-            stag[out] = (uint32_t)(lo + vbuf[slot]);
         }
     }
+    if (len == 0) return;
+    auto load = [&](int64_t e) { return KeyTraits<DT>::phi(keys[lo + e]); };
+    auto emit = [&](uint32_t pos, K key, uint32_t slot) {
+        if ((pos + 1) % x == 0) {
+            const int64_t j = (pos + 1) / x;
+            sphi[k * s + (j - 1)] = key;
+            stag[k * s + (j - 1)] = (uint32_t)(lo + slot);
+        }
+    };
+    if (!SS::run(sm, buf, slots, len, load, emit) && threadIdx.x == 0 && blockIdx.x % CL == 0)
+        atomicExch(too_big, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -159,30 +141,46 @@ lsd_upsweep_kernel(const LsdBuffers<K> b, int64_t S, int pass, const int32_t *ta
     for (int d = threadIdx.x; d < 256; d += blockDim.x) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
 }
 
-// exclusive scan of counts (digit-major) in place; one CTA
-__global__ void __launch_bounds__(1024) lsd_scan_kernel(uint32_t *counts, int64_t len, int pass,
-                                                        const int32_t *table) {
+// Exclusive scan of the per-tile counts of one digit (CTA d scans digit d)
+// plus the number of records with a smaller digit.
+__global__ void __launch_bounds__(256) lsd_scan_kernel(uint32_t *counts, int64_t tiles, int pass,
+                                                       const int32_t *table, const uint32_t *hist) {
     if (pass >= table[0]) return;
     __shared__ uint32_t tmp[40];
-    const int64_t per = (len + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per, hi = min(len, lo + per);
+    __shared__ uint32_t dbase;
+    const int q = table[1 + 3 * pass];
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t below = tid < d ? hist[q * 256 + tid] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+    if (lane == 0) tmp[warp] = below;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += tmp[w];
+        dbase = t;
+    }
+    __syncthreads();
+    uint32_t *c = counts + (int64_t)d * tiles;
+    const int64_t per = (tiles + 255) / 256;
+    const int64_t lo = tid * per, hi = imin64(tiles, lo + per);
     uint32_t local = 0;
-    for (int64_t i = lo; i < hi; ++i) local += counts[i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i = lo; i < hi; ++i) local += c[i];
     uint32_t wt;
     const uint32_t we = warp_excl_scan(local, &wt);
+    __syncthreads();
     if (lane == 31) tmp[warp] = wt;
     __syncthreads();
     if (warp == 0) {
         uint32_t t;
-        const uint32_t e = warp_excl_scan(tmp[lane], &t);
-        tmp[lane] = e;
+        const uint32_t e = warp_excl_scan(lane < 8 ? tmp[lane] : 0u, &t);
+        if (lane < 8) tmp[lane] = e;
     }
     __syncthreads();
-    uint32_t run = tmp[warp] + we;
+    uint32_t run = dbase + tmp[warp] + we;
     for (int64_t i = lo; i < hi; ++i) {
-        const uint32_t v = counts[i];
-        counts[i] = run;
+        const uint32_t v = c[i];
+        c[i] = run;
         run += v;
     }
 }
@@ -261,7 +259,7 @@ __global__ void splitter_kernel(LsdBuffers<K> b, const int32_t *table, int npos,
 }
 
 template <typename K>
-__global__ void lut_kernel(const K *vphi, const LutParams<K> *lutp, uint32_t *lut) {
+__global__ void lut_kernel(const K *vphi, const LutParams<K> *lutp, uint16_t *lut) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > kLutCells) return;
     const LutParams<K> lp = *lutp;
@@ -276,7 +274,7 @@ __global__ void lut_kernel(const K *vphi, const LutParams<K> *lutp, uint32_t *lu
             else hi = mid;
         }
     }
-    lut[c] = lo;
+    lut[c] = (uint16_t)lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -318,7 +316,7 @@ __global__ void splitter_records_kernel(const K *vphi, const uint32_t *vtag, int
 template <int DT>
 __global__ void bucket_of_kernel(const typename KeyTraits<DT>::T *keys, int64_t n, int64_t B,
                                  const typename KeyTraits<DT>::T *vphi, const uint32_t *vtag,
-                                 const uint32_t *lut,
+                                 const uint16_t *lut,
                                  const LutParams<typename KeyTraits<DT>::T> *lutp, int32_t *out) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
@@ -329,7 +327,7 @@ __global__ void bucket_of_kernel(const typename KeyTraits<DT>::T *keys, int64_t 
 
 template <typename K>
 __global__ void pad_sizes_kernel(int64_t n, int64_t R, int64_t m, int64_t M, int64_t B, const K *vphi,
-                                 const uint32_t *vtag, const uint32_t *lut, const LutParams<K> *lutp,
+                                 const uint32_t *vtag, const uint16_t *lut, const LutParams<K> *lutp,
                                  unsigned long long *out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= R * M) return;
@@ -356,14 +354,15 @@ template <int DT> static LsdBuffers<typename KeyTraits<DT>::T> lsd_buffers(const
 
 template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const Ctx &c) {
     using K = typename KeyTraits<DT>::T;
-    using CS = ClusterSort<K, true, kSortThreads, ITEMS, CL>;
-    const size_t smem = ((sizeof(typename CS::Smem) + 15) & ~size_t(15)) + CS::CAP * (sizeof(K) + 4);
+    using SS = SegSort<K, true, CL, ITEMS>;
+    const size_t smem = SS::smem_bytes();
     auto kern = run_sample_kernel<DT, CL, ITEMS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const Plan &p = c.pl;
     kern<<<(unsigned)(p.R * CL), kSortThreads, smem, c.stream>>>(
-        (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0]);
+        (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0],
+        (uint32_t *)&c.ly.status->run_too_big);
     return cudaGetLastError();
 }
 
@@ -409,7 +408,8 @@ template <typename K> static cudaError_t launch_sample_sort_t(const Ctx &c, LsdB
     for (int pass = 0; pass < NPOS && tiles > 0; ++pass) {
         lsd_upsweep_kernel<K><<<tiles, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
                                                                   c.ly.lsd_counts, p.lsd_tiles);
-        lsd_scan_kernel<<<1, 1024, 0, c.stream>>>(c.ly.lsd_counts, p.lsd_tiles * 256, pass, c.ly.lsd_table);
+        lsd_scan_kernel<<<256, 256, 0, c.stream>>>(c.ly.lsd_counts, p.lsd_tiles, pass, c.ly.lsd_table,
+                                                   c.ly.lsd_hist);
         lsd_downsweep_kernel<K><<<tiles, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
                                                                     c.ly.lsd_counts, p.lsd_tiles);
     }

@@ -34,14 +34,14 @@ class GpuResult:
 
 
 def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_pct=0,
-            debug=True, bucket_of=None):
+            debug=True, bucket_of=None, classify=0):
     """Sort with the library; returns keys, vals, sizes, sample, splitters, bucket_of, pads, stats."""
     import torch
     bsps = lib()
     n = keys.shape[0]
     code = code_of(keys)
     prm = bsps.make_params(p, s=s, runs=runs, sampling=mode, seed=seed, refine=refine,
-                           capacity_pct=capacity_pct)
+                           capacity_pct=capacity_pct, classify=classify)
     pl = bsps.bsps_get_plan(n, code, prm, vals is not None)
     ws = torch.empty(max(pl.workspace_bytes, 1), dtype=torch.uint8, device="cuda:0")
     kin = to_dev(keys)
@@ -55,8 +55,11 @@ def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_
     spl = torch.empty((max(p - 1, 1) * rec_bytes,), dtype=torch.uint8, device="cuda:0") if debug else None
     bo = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda:0") if (debug and want_bo) else None
     pads = torch.full((p,), -1, dtype=torch.int64, device="cuda:0") if debug else None
+    mlp_params = torch.zeros(bsps.MLP_PARAMS, dtype=torch.float32, device="cuda:0") if classify else None
+    mlp_loss = torch.zeros(2, dtype=torch.float32, device="cuda:0") if classify else None
     rc = bsps.bsps_sort_debug(kin, vin, kout, vout, n, code, prm, sizes, ws, sample=sample,
-                              splitters=spl, bucket_of=bo, pad_sizes=pads)
+                              splitters=spl, bucket_of=bo, pad_sizes=pads, mlp_params=mlp_params,
+                              mlp_loss=mlp_loss)
     assert rc == 0, bsps.bsps_strerror(rc)
     st = bsps.bsps_read_stats(ws)
     r = GpuResult()
@@ -69,6 +72,8 @@ def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_
     r.splitters = spl.cpu().numpy()[: (p - 1) * rec_bytes].view(oracle.RECORD_DTYPE) if debug else None
     r.bucket_of = bo.cpu().numpy()[:n] if bo is not None else None
     r.pad_sizes = pads.cpu().numpy() if debug else None
+    r.mlp_params = mlp_params.cpu().numpy() if classify else None
+    r.mlp_loss = mlp_loss.cpu().numpy() if classify else None
     return r
 
 

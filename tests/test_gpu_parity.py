@@ -162,3 +162,39 @@ def test_config2_random_2e26(name):
     ref = oracle.sort(keys, p, 0, 0, oracle.RANDOM, 1, want_sample=True)
     gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 1, bucket_of=False)
     assert_same(gpu, ref)
+
+
+def _two_close_values_and_outliers(n):
+    keys = np.full(n, 1000, np.int32)
+    keys[1::2] = 1001
+    keys[:: max(1, n // 10)] = 2**30 + np.arange(len(keys[:: max(1, n // 10)]), dtype=np.int32)
+    return keys
+
+
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_segment_split_fallback(pairs, mode):
+    """One split bin holds two distinct keys and more keys than a CTA holds:
+    the cluster falls back to full LSD passes through distributed shared memory
+    (bucket sort in random mode, block sort of the regular sample in regular mode)."""
+    n = 80_000
+    keys = _two_close_values_and_outliers(n)
+    vals = np.arange(n, dtype=np.uint32) if pairs else None
+    if mode == oracle.RANDOM:
+        ref = ref_sort(keys, 1, 8, 0, mode, 3, vals)
+        gpu = run_gpu(keys, 1, 8, 0, mode, 3, vals, refine=1)
+    else:
+        ref = ref_sort(keys, 2, 4, 1, mode, 0, vals)
+        gpu = run_gpu(keys, 2, 4, 1, mode, 0, vals)
+    assert_same(gpu, ref)
+
+
+def test_zipf_pairs_regular_p4096_2e24():
+    """The duplicate-heavy regular configuration at 1/16 of its size:
+    p = R = s = 4096 (x = 1 here), Zipf(1.1) on 256 values, payload = index."""
+    n, p = 1 << 24, 4096
+    keys = gen.zipf(n, seed=3)
+    vals = np.arange(n, dtype=np.uint32)
+    ref = oracle.sort(keys, p, p, p, oracle.REGULAR, 0, vals=vals, want_sample=True)
+    gpu = run_gpu(keys, p, p, p, oracle.REGULAR, 0, vals, bucket_of=False)
+    assert_same(gpu, ref)
