@@ -209,6 +209,34 @@ int bsps_mlp_workspace_size(int64_t m, size_t *bytes);
 int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y, int64_t m, float *d_grad,
                        float *d_loss, void *d_ws, size_t ws_bytes, void *stream);
 
+/*
+ * bsps_sort_keys_noalloc -- bsps_sort_keys without a caller workspace.
+ *
+ * No counterpart in the paper.  It is for callers that cannot allocate
+ * device memory themselves: code whose device memory belongs to another
+ * runtime or framework that exposes no allocator to it, or latency-critical
+ * code that must never call cudaMalloc (which may synchronize the device).
+ * Instead of d_ws it uses a scratch array of BSPS_NOALLOC_SCRATCH_BYTES that
+ * the library declares statically in device memory; every GPU that loads the
+ * library holds that array until the process exits.
+ *
+ * Arguments and results are those of bsps_sort_keys.  The largest accepted
+ * problem is the one whose bsps_workspace_size() (keys only) fits the scratch
+ * (for int32 keys with p = 256 and random oversampling, about 2^23 keys);
+ * anything larger returns BSPS_ERR_TOO_LARGE before any work is queued.  The
+ * call allocates nothing (no cudaMalloc, no cudaFree).  The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress, once
+ * per device, with that device current); make that first call before any
+ * stream capture.  All calls in the process share the one scratch array, which
+ * keeps the previous call's contents: the call clears what must start at zero
+ * itself, and calls whose executions overlap on the GPU (different streams,
+ * or different host threads without ordering) race on it and must not be
+ * issued.  Device-side statistics of these calls are not exposed.
+ */
+#define BSPS_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, int64_t n, int32_t dtype,
+                           const bsps_params *prm, int64_t *d_bucket_sizes, void *stream);
+
 /* bsps_strerror -- static text for a status code. */
 const char *bsps_strerror(int status);
 

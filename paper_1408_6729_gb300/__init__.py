@@ -27,7 +27,8 @@ BSPS_ERR_TOO_LARGE = -7
 
 EXPORTS = ["bsps_get_plan", "bsps_workspace_size", "bsps_sort_keys", "bsps_sort_pairs",
            "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad",
-           "bsps_strerror"]
+           "bsps_sort_keys_noalloc", "bsps_strerror"]
+BSPS_NOALLOC_SCRATCH_BYTES = 64 << 20
 MLP_PARAMS = 1153
 
 
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
     lib.bsps_read_stats.argtypes = [P, ctypes.POINTER(bsps_stats), P]
     lib.bsps_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
     lib.bsps_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, SZ, P]
+    lib.bsps_sort_keys_noalloc.argtypes = [P, P, I64, I32, PP, P, P]
     lib.bsps_strerror.argtypes = [ctypes.c_int]
     lib.bsps_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -160,6 +162,13 @@ def bsps_workspace_size(n, dtype, params, with_payload=False) -> int:
 def bsps_sort_keys(keys_in, keys_out, n, dtype, params, bucket_sizes, workspace, stream=None) -> int:
     return load().bsps_sort_keys(_ptr(keys_in), _ptr(keys_out), int(n), int(dtype), ctypes.byref(params),
                                  _ptr(bucket_sizes), _ptr(workspace), _nbytes(workspace), _stream(stream))
+
+
+def bsps_sort_keys_noalloc(keys_in, keys_out, n, dtype, params, bucket_sizes, stream=None) -> int:
+    """bsps_sort_keys for callers that cannot allocate: the library's static
+    device scratch replaces the workspace (see include/bspsort.h)."""
+    return load().bsps_sort_keys_noalloc(_ptr(keys_in), _ptr(keys_out), int(n), int(dtype), ctypes.byref(params),
+                                         _ptr(bucket_sizes), _stream(stream))
 
 
 def bsps_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, dtype, params, bucket_sizes, workspace,
