@@ -205,7 +205,8 @@ def run_gpu(args, wl, name):
     lib_build.build()  # no-op once built
     n, p = wl["n"], wl["p"]
     code = bsps.BSPS_I32
-    prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank)
+    prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
+                           refine=args.refine)
     plan = bsps.bsps_get_plan(n, code, prm, wl["pairs"])
     keys_h = wl["make"](n, p, 1 + rank)
     kin = torch.from_numpy(keys_h).to(dev)
@@ -356,6 +357,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg (profiling runs)")
+    ap.add_argument("--refine", type=int, default=0, help="sub-buckets per bucket (0: the library's choice)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

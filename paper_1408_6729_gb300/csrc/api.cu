@@ -18,9 +18,10 @@ static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-static int items_for(int key_bytes, bool slot) {
-    if (slot) return key_bytes == 8 ? kPairItems64 : kPairItems32;
-    return key_bytes == 8 ? kBucketItems64 : kBucketItems32;
+// keys one CTA of the sub-bucket sort holds
+static int64_t cta_capacity(int key_bytes, bool slot) {
+    if (slot) return (int64_t)kSortThreads * (key_bytes == 8 ? kPairItems64 : kPairItems32);
+    return (int64_t)512 * (key_bytes == 8 ? kKeysItems64 : kKeysItems32);
 }
 
 // Resolve the parameters and the internal layout.  Defaults follow Sec. 6.1:
@@ -73,7 +74,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
 
     // sub-buckets: the smallest refinement whose expected size fits one
     // cluster's shared memory with head room for the sampling imbalance
-    const int64_t cap_cta = (int64_t)kSortThreads * items_for(pl.key_bytes, pairs);
+    const int64_t cap_cta = cta_capacity(pl.key_bytes, pairs);
     auto headroom = [&](int64_t B) {
         return pl.sampling == BSPS_RANDOM ? 1.0 + 5.0 / std::sqrt((double)std::max<int64_t>(1, pl.Q / B))
                                           : 1.25;
@@ -109,6 +110,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         pl.cap = std::min<int64_t>(std::max<int64_t>(n, 1), (int64_t)std::ceil((double)n / pl.P * pct) + 64);
         pl.run_cl = 1;
     }
+    pl.cap = (pl.cap + 3) & ~int64_t(3);  // 16-byte aligned regions
     if ((double)pl.P * pl.cap >= 4.0e9) return BSPS_ERR_TOO_LARGE;
     pl.tiles = (n + kRouteTile - 1) / kRouteTile;
     pl.lsd_tiles = (pl.sample_size + kLsdTile - 1) / kLsdTile;
@@ -132,7 +134,8 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
     take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
     take(pl.P * 4);
-    take(pl.P * pl.cap * pl.key_bytes);
+    take(pl.P * 4); take(pl.P * 4);
+    take(pl.P * pl.cap * pl.key_bytes + 64);
     take(pairs ? pl.P * pl.cap * 4 : 0);
     take(pl.P * 4);
     take((pl.P + 1) * 8);
@@ -169,7 +172,9 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.state = (uint32_t *)take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
     l.ids = (uint16_t *)take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
     l.cursor = (uint32_t *)take(pl.P * 4);
-    l.reg_keys = take(pl.P * pl.cap * pl.key_bytes);
+    l.retry_flag = (uint32_t *)take(pl.P * 4);
+    l.retry_list = (uint32_t *)take(pl.P * 4);
+    l.reg_keys = take(pl.P * pl.cap * pl.key_bytes + 64);
     l.reg_vals = (uint32_t *)take(pl.pairs ? pl.P * pl.cap * 4 : 0);
     l.vsize = (uint32_t *)take(pl.P * 4);
     l.voff = (uint64_t *)take((pl.P + 1) * 8);
@@ -206,7 +211,7 @@ static int kernels_per_call(const Plan &pl) {
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
-    k += 2;                                      // cluster bucket sort, out-of-core bucket sort
+    k += pl.pairs ? 2 : 3;                       // cluster bucket sort tiers, out-of-core bucket sort
     if (pl.classify == BSPS_LEARNED) k += 3;     // training set, initial weights, training
     return k;
 }
@@ -258,6 +263,7 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     auto mark = [&](int i) { return ev ? cudaEventRecord((cudaEvent_t)ev[i], c.stream) : cudaSuccess; };
     if (c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
     BSPS_CUDA(cudaMemsetAsync(c.ly.cursor, 0, (size_t)c.pl.P * 4, c.stream));
+    if (!c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.retry_flag, 0, (size_t)c.pl.P * 4, c.stream));
     BSPS_CUDA(mark(0));
     BSPS_CUDA(launch_sample(c));
     BSPS_CUDA(mark(1));

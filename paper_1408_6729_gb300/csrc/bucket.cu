@@ -1,10 +1,16 @@
 // bucket.cu -- final sort of every bucket (Fig. 2 step 12 / Fig. 3 step 14):
 // the keys a bucket received, in input order, are sorted stably and written
 // to the bucket's place in the output.  Each sub-bucket is sorted on chip by
-// one thread-block cluster; sub-buckets larger than the cluster's shared
-// memory go to an out-of-core radix sort in global memory.
+// one thread-block cluster, in up to three tiers:
+//   1. keys only: the throughput sort of segsort_keys.cuh (unstable ranks,
+//      which equal keys cannot reveal);
+//   2. with payloads, or what tier 1 gives back: the stable cluster sort of
+//      segsort.cuh;
+//   3. sub-buckets larger than a cluster's shared memory: an out-of-core
+//      radix sort in global memory.
 #include "kernels.cuh"
 #include "segsort.cuh"
+#include "segsort_keys.cuh"
 
 namespace bsps {
 
@@ -18,6 +24,12 @@ template <typename K> struct BucketArgs {
     uint32_t *out_vals;
     uint32_t *slow_list;
     DevStatus *st;
+    const K *vphi;            // sub-bucket splitters (bounds of every sub-bucket)
+    int64_t P;
+    uint32_t *retry_flag;     // tier 1 gave the sub-bucket back
+    uint32_t *retry_list;
+    const uint32_t *only;     // tier 2 over a list (nullable: every sub-bucket)
+    const int32_t *only_count;
 };
 
 template <int DT, bool PAIRS, int CL, int ITEMS>
@@ -30,22 +42,57 @@ bucket_sort_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
     uint32_t *slots = reinterpret_cast<uint32_t *>(buf + SS::CAP);
 
+    // every sub-bucket (one per cluster), or the listed ones (clusters loop)
+    const int64_t nitems = a.only ? *a.only_count : a.P;
+    const int64_t clusters = gridDim.x / CL;
+    for (int64_t it = blockIdx.x / CL; it < nitems; it += (a.only ? clusters : nitems)) {
+        const int64_t v = a.only ? a.only[it] : it;
+        const int64_t cnt = imin64(a.vsize[v], a.cap);
+        if (cnt == 0) continue;
+        const uint64_t off = a.voff[v];
+        const K *src = a.reg_keys + v * a.cap;
+        const uint32_t *vsrc = a.reg_vals + v * a.cap;
+        K *out_k = a.out_keys + off;
+        uint32_t *out_v = a.out_vals + off;
+        auto emit = [&](uint32_t pos, K key, uint32_t slot) {
+            out_k[pos] = KeyTraits<DT>::inv(key);
+            if constexpr (PAIRS) out_v[pos] = vsrc[slot];
+        };
+        const bool done = SS::run(sm, buf, slots, cnt, [&](int64_t e) { return src[e]; }, emit);
+        if (!done && blockIdx.x % CL == 0 && threadIdx.x == 0) {
+            const int slot = atomicAdd(&a.st->slow_buckets, 1);
+            a.slow_list[slot] = (uint32_t)v;
+        }
+        // the next sub-bucket reuses every CTA's shared memory
+        if (a.only) cg::this_cluster().sync();
+        else __syncthreads();
+    }
+}
+
+// Tier 1 (keys only): one cluster per sub-bucket; its bounds are the two
+// splitters around it (the smallest and largest key for the end buckets).
+template <int DT, int CL, int ITEMS>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
+bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
+    using K = typename KeyTraits<DT>::T;
+    using SS = SegSortKeys<K, CL, ITEMS>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
+    K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
+    uint16_t *rk = reinterpret_cast<uint16_t *>(buf + SS::CAP);
+
     const int64_t v = blockIdx.x / CL;
     const int64_t cnt = imin64(a.vsize[v], a.cap);
     if (cnt == 0) return;
-    const uint64_t off = a.voff[v];
-    const K *src = a.reg_keys + v * a.cap;
-    const uint32_t *vsrc = a.reg_vals + v * a.cap;
-    K *out_k = a.out_keys + off;
-    uint32_t *out_v = a.out_vals + off;
-    auto emit = [&](uint32_t pos, K key, uint32_t slot) {
-        out_k[pos] = KeyTraits<DT>::inv(key);
-        if constexpr (PAIRS) out_v[pos] = vsrc[slot];
-    };
-    const bool done = SS::run(sm, buf, slots, cnt, [&](int64_t e) { return src[e]; }, emit);
-    if (!done && blockIdx.x % CL == 0 && threadIdx.x == 0) {
-        const int slot = atomicAdd(&a.st->slow_buckets, 1);
-        a.slow_list[slot] = (uint32_t)v;
+    const K lo = v > 0 ? a.vphi[v - 1] : (K)~a.st->ext_min_inv;
+    const K hi = v < a.P - 1 ? a.vphi[v] : (K)a.st->ext_max;
+    K *out_k = a.out_keys + a.voff[v];
+    auto emit = [&](uint32_t pos, K key) { out_k[pos] = KeyTraits<DT>::inv(key); };
+    if (!SS::run(sm, buf, rk, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
+        if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
+            const int slot = atomicAdd(&a.st->retry_count, 1);
+            a.retry_list[slot] = (uint32_t)v;
+        }
     }
 }
 
@@ -144,14 +191,28 @@ __global__ void __launch_bounds__(kSlowThreads) bucket_slow_kernel(BucketArgs<ty
     }
 }
 
-template <int DT, bool PAIRS, int CL, int ITEMS> static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
+template <int DT, bool PAIRS, int CL, int ITEMS>
+static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a, bool listed) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSort<K, PAIRS, CL, ITEMS>;
     const size_t smem = SS::smem_bytes();
     auto kern = bucket_sort_kernel<DT, PAIRS, CL, ITEMS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(c.pl.P * CL), 1024, smem, c.stream>>>(a);
+    const int64_t clusters = listed ? imin64(16, c.pl.P) : c.pl.P;
+    kern<<<(unsigned)(clusters * CL), 1024, smem, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT, int CL, int ITEMS>
+static cudaError_t launch_keys(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
+    using K = typename KeyTraits<DT>::T;
+    using SS = SegSortKeys<K, CL, ITEMS>;
+    const size_t smem = SS::smem_bytes();
+    auto kern = bucket_keys_kernel<DT, CL, ITEMS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(c.pl.P * CL), 512, smem, c.stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -167,15 +228,37 @@ template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
     a.out_vals = c.vals_out;
     a.slow_list = c.ly.slow_list;
     a.st = c.ly.status;
+    a.vphi = (const K *)c.ly.vphi;
+    a.P = c.pl.P;
+    a.retry_flag = c.ly.retry_flag;
+    a.retry_list = c.ly.retry_list;
+    a.only = nullptr;
+    a.only_count = nullptr;
     constexpr int IT = PAIRS ? (sizeof(K) == 8 ? kPairItems64 : kPairItems32)
                              : (sizeof(K) == 8 ? kBucketItems64 : kBucketItems32);
-    cudaError_t e;
-    switch (c.pl.bucket_cl) {
-    case 1: e = launch_cluster<DT, PAIRS, 1, IT>(c, a); break;
-    case 2: e = launch_cluster<DT, PAIRS, 2, IT>(c, a); break;
-    case 4: e = launch_cluster<DT, PAIRS, 4, IT>(c, a); break;
-    case 8: e = launch_cluster<DT, PAIRS, 8, IT>(c, a); break;
-    default: return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if constexpr (!PAIRS) {
+        constexpr int KIT = sizeof(K) == 8 ? kKeysItems64 : kKeysItems32;
+        switch (c.pl.bucket_cl) {
+        case 1: e = launch_keys<DT, 1, KIT>(c, a); break;
+        case 2: e = launch_keys<DT, 2, KIT>(c, a); break;
+        case 4: e = launch_keys<DT, 4, KIT>(c, a); break;
+        case 8: e = launch_keys<DT, 8, KIT>(c, a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+        // what tier 1 gave back: the stable cluster sort over the list
+        a.only = c.ly.retry_list;
+        a.only_count = &c.ly.status->retry_count;
+        e = launch_cluster<DT, false, 8, IT>(c, a, true);
+    } else {
+        switch (c.pl.bucket_cl) {
+        case 1: e = launch_cluster<DT, PAIRS, 1, IT>(c, a, false); break;
+        case 2: e = launch_cluster<DT, PAIRS, 2, IT>(c, a, false); break;
+        case 4: e = launch_cluster<DT, PAIRS, 4, IT>(c, a, false); break;
+        case 8: e = launch_cluster<DT, PAIRS, 8, IT>(c, a, false); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     if (e != cudaSuccess) return e;
     bucket_slow_kernel<DT, PAIRS><<<64, kSlowThreads, 0, c.stream>>>(a, (K *)c.ly.reg_keys, c.ly.reg_vals);

@@ -23,7 +23,8 @@ __device__ __forceinline__ uint32_t classify_key(K phi, uint32_t tag, const LutP
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         const K sp = sphi[mid];
-        const bool le = sp < phi || (sp == phi && stag[mid] <= tag);
+        bool le = sp < phi;
+        if (sp == phi) le = stag[mid] <= tag;  // tags are read on ties only
         lo = le ? mid + 1 : lo;
         hi = le ? hi : mid;
     }

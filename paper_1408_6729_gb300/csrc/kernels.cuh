@@ -33,6 +33,8 @@ constexpr int kBucketItems32 = 14;     // sub-bucket sort, keys only, 4-byte key
 constexpr int kBucketItems64 = 10;     // ... 8-byte keys
 constexpr int kPairItems32 = 12;       // sub-bucket sort with payload slots, 4-byte keys
 constexpr int kPairItems64 = 8;        // ... 8-byte keys
+constexpr int kKeysItems32 = 24;       // throughput keys-only sort: 512 threads x 24 = 12288 keys per CTA
+constexpr int kKeysItems64 = 12;       // ... 8-byte keys
 constexpr int kSlowThreads = 512;      // out-of-core sort of an oversized sub-bucket
 constexpr int kSlowItems = 8;
 
@@ -81,6 +83,8 @@ struct Layout {
     uint32_t *state;        // tiles * P lookback words
     uint16_t *ids;          // tiles * kRouteTile sub-bucket ids (routing scratch)
     uint32_t *cursor;       // P keys routed per sub-bucket
+    uint32_t *retry_flag;   // P: the keys-only sort gave the sub-bucket back
+    uint32_t *retry_list;   // P
     // learned classifier (classify == BSPS_LEARNED)
     float *mlp_params, *mlp_m, *mlp_v;   // 1153 each
     float *mlp_part;                     // training grid x 1154 partial sums

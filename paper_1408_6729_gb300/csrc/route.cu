@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     __syncthreads();
     const LutParams<K> lp = fx.lp;
     const int bbits = bit_length<uint32_t>(P);  // sub-bucket ids, with P as "no key"
+    // smallest and largest key: the outer bounds of the first and last
+    // sub-bucket for the keys-only bucket sort
+    K kmin = all_ones<K>(), kmax = K(0);
 
     for (;;) {
         if (tid == 0) fx.tile = (int64_t)atomicAdd(&a.st->tile_counter, 1u);
@@ -154,9 +157,21 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                         b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), mw, *mnorm, P, sphi, stag, steps);
                         n_mis += steps > 0;
                         n_steps += steps;
+                        if constexpr (!PAIRS) {
+                            const K ph = KeyTraits<DT>::phi(kk[i]);
+                            kmin = ph < kmin ? ph : kmin;
+                            kmax = ph > kmax ? ph : kmax;
+                        }
                     }
                 } else {
-                    if (ok) b = classify_key(KeyTraits<DT>::phi(kk[i]), (uint32_t)(t0 + e), lp, lut, sphi, stag);
+                    if (ok) {
+                        const K ph = KeyTraits<DT>::phi(kk[i]);
+                        b = classify_key(ph, (uint32_t)(t0 + e), lp, lut, sphi, stag);
+                        if constexpr (!PAIRS) {
+                            kmin = ph < kmin ? ph : kmin;
+                            kmax = ph > kmax ? ph : kmax;
+                        }
+                    }
                 }
                 // keys of lane 0's bucket are counted with one atomic (runs
                 // of equal buckets are common in skewed inputs)
@@ -381,6 +396,18 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
         }
         // the sub-bucket ids of this tile are dead: drop them from L2 unwritten
         for (int64_t line = tid; line * 64 < tlen; line += TH) discard_l2_line(ids + line * 64);
+    }
+    if constexpr (!PAIRS) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const K x = __shfl_xor_sync(0xffffffffu, kmin, o), y = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmin = x < kmin ? x : kmin;
+            kmax = y > kmax ? y : kmax;
+        }
+        if (lane == 0 && kmin <= kmax) {
+            atomicMax(&a.st->ext_min_inv, ~(unsigned long long)kmin);
+            atomicMax(&a.st->ext_max, (unsigned long long)kmax);
+        }
     }
     if constexpr (LEARNED) {  // misprediction statistics of the learned classifier
         const uint32_t m = __reduce_add_sync(0xffffffffu, n_mis), st = __reduce_add_sync(0xffffffffu, n_steps);
