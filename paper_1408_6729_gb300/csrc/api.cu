@@ -131,8 +131,8 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(pl.P * 4);
     take((kLutCells + 2) * 2);
     take(64);
-    take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
-    take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
+    take(pairs ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
+    take(pairs ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     take(pl.P * 4);
     take(pl.P * 4); take(pl.P * 4);
     take(pl.P * pl.cap * pl.key_bytes + 64);
@@ -169,8 +169,8 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.vtag = (uint32_t *)take(pl.P * 4);
     l.lut = (uint16_t *)take((kLutCells + 2) * 2);
     l.lutp = take(64);
-    l.state = (uint32_t *)take(std::max<int64_t>(pl.tiles, 1) * pl.P * 4);
-    l.ids = (uint16_t *)take(std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2);
+    l.state = (uint32_t *)take(pl.pairs ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
+    l.ids = (uint16_t *)take(pl.pairs ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     l.cursor = (uint32_t *)take(pl.P * 4);
     l.retry_flag = (uint32_t *)take(pl.P * 4);
     l.retry_list = (uint32_t *)take(pl.P * 4);

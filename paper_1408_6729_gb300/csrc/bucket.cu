@@ -77,10 +77,6 @@ bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSortKeys<K, CL, ITEMS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
-    K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
-    uint16_t *rk = reinterpret_cast<uint16_t *>(buf + SS::CAP);
-
     const int64_t v = blockIdx.x / CL;
     const int64_t cnt = imin64(a.vsize[v], a.cap);
     if (cnt == 0) return;
@@ -88,7 +84,7 @@ bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     const K hi = v < a.P - 1 ? a.vphi[v] : (K)a.st->ext_max;
     K *out_k = a.out_keys + a.voff[v];
     auto emit = [&](uint32_t pos, K key) { out_k[pos] = KeyTraits<DT>::inv(key); };
-    if (!SS::run(sm, buf, rk, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
+    if (!SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
         if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
             const int slot = atomicAdd(&a.st->retry_count, 1);
             a.retry_list[slot] = (uint32_t)v;

@@ -33,8 +33,8 @@ constexpr int kBucketItems32 = 14;     // sub-bucket sort, keys only, 4-byte key
 constexpr int kBucketItems64 = 10;     // ... 8-byte keys
 constexpr int kPairItems32 = 12;       // sub-bucket sort with payload slots, 4-byte keys
 constexpr int kPairItems64 = 8;        // ... 8-byte keys
-constexpr int kKeysItems32 = 24;       // throughput keys-only sort: 512 threads x 24 = 12288 keys per CTA
-constexpr int kKeysItems64 = 12;       // ... 8-byte keys
+constexpr int kKeysItems32 = 20;       // throughput keys-only sort: 512 threads x 20 = 10240 keys per CTA
+constexpr int kKeysItems64 = 10;       // ... 8-byte keys
 constexpr int kSlowThreads = 512;      // out-of-core sort of an oversized sub-bucket
 constexpr int kSlowItems = 8;
 
@@ -125,5 +125,7 @@ cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: trainin
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);
+cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
+size_t route_keys_smem_bytes(const Plan &pl);
 
 } // namespace bsps

@@ -1,16 +1,17 @@
 // route.cu -- classification, per-bucket prefix and the routing permutation
-// (Fig. 1 steps 9-11; Fig. 2 steps 9-11), then the bucket offsets.
+// for keys with payloads (Fig. 1 steps 9-11; Fig. 2 steps 9-11), then the
+// bucket offsets for both paths.
 //
 // One pass over the keys in HBM.  Tiles of kRouteTile keys are taken in
 // order from an atomic ticket.  A tile first counts its keys per sub-bucket
 // (Fig. 1 step 9), publishes the counts, and finds how many keys of each
 // sub-bucket come before it by looking back over earlier tiles' published
-// counts (decoupled look-back: the "p independent parallel prefix
-// operations" of Fig. 1 step 9, Lemma 4.2).  It then reads its keys again
-// (from L2), stably sorts each chunk by sub-bucket in shared memory, and
-// writes each sub-bucket's keys as one contiguous run into that sub-bucket's
-// region.  Keys keep input order inside every region (Fig. 1 step 11: "the
-// initial ordering of the keys is preserved").
+// counts (a decoupled look-back computes the per-bucket prefix sums of
+// Fig. 1 step 9, Lemma 4.2).  It then reads its keys again (from L2), stably
+// sorts each chunk by sub-bucket in shared memory, and writes each
+// sub-bucket's keys as one contiguous run into that sub-bucket's region.
+// Inside every region keys keep their input order (Fig. 1 step 11), which
+// makes the final per-bucket sort stable.
 #include "classify.cuh"
 #include "mlp.cuh"
 #include "radix.cuh"
@@ -54,8 +55,8 @@ template <typename K> struct RouteFixed {
 // Shared memory of the routing kernel.  The splitters' phi live in shared
 // memory when they fit next to the rest, in global memory (L1-cached)
 // otherwise; their tags, read only on ties, stay in global memory.
-template <typename K, bool PAIRS, bool LEARNED = false> struct RouteSmemLayout {
-    size_t mlp, lut, sphi, run, coff, stage_k, stage_v, stage_b, total;
+template <typename K, bool LEARNED = false> struct RouteSmemLayout {
+    size_t mlp, lut, sphi, run, stage_k, stage_v, stage_b, total;
     bool sphi_in_smem;
     __host__ __device__ RouteSmemLayout(uint32_t P) {
         for (int pass = 0; pass < 2; ++pass) {
@@ -68,10 +69,9 @@ template <typename K, bool PAIRS, bool LEARNED = false> struct RouteSmemLayout {
             sphi = o;    o += sphi_in_smem ? sizeof(K) * (P > 1 ? P - 1 : 1) : 0;
             o = (o + 15) & ~size_t(15);
             run = o;     o += sizeof(uint32_t) * P;
-            coff = o;    o += PAIRS ? 0 : sizeof(uint32_t) * (P + 1);
             o = (o + 15) & ~size_t(15);
             stage_k = o; o += sizeof(K) * route_chunk<K>();
-            stage_v = o; o += PAIRS ? sizeof(uint32_t) * route_chunk<K>() : 0;
+            stage_v = o; o += sizeof(uint32_t) * route_chunk<K>();
             stage_b = o; o += sizeof(uint16_t) * route_chunk<K>();
             total = o;
             if (total <= kRouteSmemBudget) break;
@@ -83,7 +83,7 @@ __device__ __forceinline__ void discard_l2_line(const void *p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
-template <int DT, bool PAIRS, bool LEARNED>
+template <int DT, bool LEARNED>
 __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
     constexpr int IT = route_items<K>();
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     constexpr int CH = route_chunk<K>();
     using Rank = BlockRank<TH, IT, 8>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RouteSmemLayout<K, PAIRS, LEARNED> L(a.P);
+    const RouteSmemLayout<K, LEARNED> L(a.P);
     float *mw = reinterpret_cast<float *>(smem_raw + L.mlp);
     MlpNorm *mnorm = reinterpret_cast<MlpNorm *>(mw + kParams + 3);
     uint32_t n_mis = 0, n_steps = 0;
@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     const K *sphi = L.sphi_in_smem ? sphi_s : a.vphi;
     const uint32_t *stag = a.vtag;
     uint32_t *run = reinterpret_cast<uint32_t *>(smem_raw + L.run);
-    uint32_t *coff = reinterpret_cast<uint32_t *>(smem_raw + L.coff);
     K *stage_k = reinterpret_cast<K *>(smem_raw + L.stage_k);
     uint32_t *stage_v = reinterpret_cast<uint32_t *>(smem_raw + L.stage_v);
     uint16_t *stage_b = reinterpret_cast<uint16_t *>(smem_raw + L.stage_b);
@@ -113,8 +112,6 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     for (int i = tid; i <= kLutCells; i += TH) lut[i] = a.lut[i];
     if (L.sphi_in_smem)
         for (uint32_t i = tid; i < nsplit; i += TH) sphi_s[i] = a.vphi[i];
-    if constexpr (!PAIRS)
-        for (uint32_t b = tid; b <= P; b += TH) coff[b] = 0;
     if constexpr (LEARNED) {
         for (int k = tid; k < kParams; k += TH) mw[k] = a.mlp_params[k];
         if (tid == 0) *mnorm = *a.mlp_norm;
@@ -123,9 +120,6 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     __syncthreads();
     const LutParams<K> lp = fx.lp;
     const int bbits = bit_length<uint32_t>(P);  // sub-bucket ids, with P as "no key"
-    // smallest and largest key: the outer bounds of the first and last
-    // sub-bucket for the keys-only bucket sort
-    K kmin = all_ones<K>(), kmax = K(0);
 
     for (;;) {
         if (tid == 0) fx.tile = (int64_t)atomicAdd(&a.st->tile_counter, 1u);
@@ -157,21 +151,9 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                         b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), mw, *mnorm, P, sphi, stag, steps);
                         n_mis += steps > 0;
                         n_steps += steps;
-                        if constexpr (!PAIRS) {
-                            const K ph = KeyTraits<DT>::phi(kk[i]);
-                            kmin = ph < kmin ? ph : kmin;
-                            kmax = ph > kmax ? ph : kmax;
-                        }
                     }
                 } else {
-                    if (ok) {
-                        const K ph = KeyTraits<DT>::phi(kk[i]);
-                        b = classify_key(ph, (uint32_t)(t0 + e), lp, lut, sphi, stag);
-                        if constexpr (!PAIRS) {
-                            kmin = ph < kmin ? ph : kmin;
-                            kmax = ph > kmax ? ph : kmax;
-                        }
-                    }
+                    if (ok) b = classify_key(KeyTraits<DT>::phi(kk[i]), (uint32_t)(t0 + e), lp, lut, sphi, stag);
                 }
                 // keys of lane 0's bucket are counted with one atomic (runs
                 // of equal buckets are common in skewed inputs)
@@ -187,19 +169,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
         __syncthreads();
 
         // ---- where this tile's keys go inside every sub-bucket region ----
-        if constexpr (!PAIRS) {
-            // keys only: the order of equal-bucket keys inside a region is
-            // free, so each tile reserves its runs with one atomic per bucket
-            for (uint32_t b = tid; b < P; b += TH) {
-                const uint32_t c = run[b];
-                const uint32_t at = c ? atomicAdd(&a.cursor[b], c) : 0u;
-                run[b] = at;
-                if ((uint64_t)at + c > (uint64_t)a.cap) {
-                    atomicExch(&a.st->overflow, 1);
-                    set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
-                }
-            }
-        } else {
+        {
             // with payloads: input order is kept (Fig. 1 step 11), so every
             // tile needs the keys of each bucket in all earlier tiles -- the
             // p parallel prefix sums of Fig. 1 step 9 (Lemma 4.2), done as a
@@ -261,56 +231,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
         //      shared memory and every sub-bucket run is written contiguously ----
         for (int64_t cs = 0; cs < tlen; cs += CH) {
             const int clen = (int)imin64(CH, tlen - cs);
-            if constexpr (!PAIRS) {
-                // keys only: order inside a run is free, ranks come from atomics
-                K kk[IT];
-                uint32_t bb[IT], rk[IT];
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const int s = i * TH + tid;
-                    const bool ok = s < clen;
-                    kk[i] = ok ? KeyTraits<DT>::phi(a.keys[t0 + cs + s]) : K(0);
-                    bb[i] = ok ? (uint32_t)ids[cs + s] : P;
-                }
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const uint32_t b = bb[i];
-                    const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
-                    const uint32_t same = __ballot_sync(0xffffffffu, b == b0);
-                    if (b == b0) {
-                        const int leader = __ffs(same) - 1;
-                        uint32_t r0 = 0;
-                        if (lane == leader) r0 = atomicAdd(&coff[b], (uint32_t)__popc(same));
-                        r0 = __shfl_sync(same, r0, leader);
-                        rk[i] = r0 + __popc(same & lanemask_lt());
-                    } else {
-                        rk[i] = atomicAdd(&coff[b], 1u);
-                    }
-                }
-                __syncthreads();
-                block_excl_scan_smem<TH>(coff, (int)P + 1, fx.tmp);
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const uint32_t pos = coff[bb[i]] + rk[i];
-                    stage_k[pos] = kk[i];
-                    stage_b[pos] = (uint16_t)bb[i];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int i = 0; i < IT; ++i) {
-                    const int s = i * TH + tid;
-                    const uint32_t b = stage_b[s];
-                    if (b < P) {
-                        const uint32_t idx = run[b] + (uint32_t)s - coff[b];
-                        if (idx < a.cap) a.reg_keys[(int64_t)b * a.cap + idx] = stage_k[s];
-                    }
-                }
-                __syncthreads();
-                for (uint32_t b = tid; b < P; b += TH) run[b] += coff[b + 1] - coff[b];
-                __syncthreads();
-                for (uint32_t b = tid; b <= P; b += TH) coff[b] = 0;
-                __syncthreads();
-            } else {
+            {
                 // with payloads: stable partition by sub-bucket (LSD over its bits)
                 K kk[IT];
                 uint32_t vv[IT], bb[IT], d[IT], rk[IT];
@@ -397,18 +318,6 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
         // the sub-bucket ids of this tile are dead: drop them from L2 unwritten
         for (int64_t line = tid; line * 64 < tlen; line += TH) discard_l2_line(ids + line * 64);
     }
-    if constexpr (!PAIRS) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const K x = __shfl_xor_sync(0xffffffffu, kmin, o), y = __shfl_xor_sync(0xffffffffu, kmax, o);
-            kmin = x < kmin ? x : kmin;
-            kmax = y > kmax ? y : kmax;
-        }
-        if (lane == 0 && kmin <= kmax) {
-            atomicMax(&a.st->ext_min_inv, ~(unsigned long long)kmin);
-            atomicMax(&a.st->ext_max, (unsigned long long)kmax);
-        }
-    }
     if constexpr (LEARNED) {  // misprediction statistics of the learned classifier
         const uint32_t m = __reduce_add_sync(0xffffffffu, n_mis), st = __reduce_add_sync(0xffffffffu, n_steps);
         if (lane == 0 && (m | st)) {
@@ -468,7 +377,7 @@ bucket_finish_kernel(const uint32_t *cursor, uint32_t P, int64_t B, int64_t cap,
     }
 }
 
-template <int DT, bool PAIRS, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) {
+template <int DT, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) {
     using K = typename KeyTraits<DT>::T;
     const Plan &p = c.pl;
     RouteArgs<K> a;
@@ -490,8 +399,8 @@ template <int DT, bool PAIRS, bool LEARNED> static cudaError_t launch_route_t(co
     a.st = c.ly.status;
     a.mlp_params = c.ly.mlp_params;
     a.mlp_norm = c.ly.mlp_norm;
-    const size_t smem = RouteSmemLayout<K, PAIRS, LEARNED>((uint32_t)p.P).total;
-    auto kern = route_kernel<DT, PAIRS, LEARNED>;
+    const size_t smem = RouteSmemLayout<K, LEARNED>((uint32_t)p.P).total;
+    auto kern = route_kernel<DT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -500,20 +409,14 @@ template <int DT, bool PAIRS, bool LEARNED> static cudaError_t launch_route_t(co
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRouteThreads, smem);
     const int64_t grid = imin64(p.tiles, (int64_t)max(occ, 1) * sms);
     kern<<<(unsigned)grid, kRouteThreads, smem, c.stream>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    bucket_finish_kernel<<<1, 1024, 0, c.stream>>>(c.ly.cursor, (uint32_t)p.P, p.B, p.cap, c.ly.vsize, c.ly.voff,
-                                                   c.bucket_sizes, c.ly.status);
     return cudaGetLastError();
 }
 
 template <int DT> static cudaError_t launch_route_d(const Ctx &c) {
-    const bool pr = c.pl.pairs != 0, learned = c.pl.classify == BSPS_LEARNED;
-    if (learned) return pr ? launch_route_t<DT, true, true>(c) : launch_route_t<DT, false, true>(c);
-    return pr ? launch_route_t<DT, true, false>(c) : launch_route_t<DT, false, false>(c);
+    return c.pl.classify == BSPS_LEARNED ? launch_route_t<DT, true>(c) : launch_route_t<DT, false>(c);
 }
 
-cudaError_t launch_route(const Ctx &c) {
+static cudaError_t launch_route_pairs(const Ctx &c) {
     switch (c.pl.dtype) {
     case BSPS_U32: return launch_route_d<BSPS_U32>(c);
     case BSPS_I32: return launch_route_d<BSPS_I32>(c);
@@ -522,15 +425,21 @@ cudaError_t launch_route(const Ctx &c) {
     }
 }
 
+cudaError_t launch_route(const Ctx &c) {
+    cudaError_t e = c.pl.pairs ? launch_route_pairs(c) : launch_route_keys(c);
+    if (e != cudaSuccess) return e;
+    const Plan &p = c.pl;
+    bucket_finish_kernel<<<1, 1024, 0, c.stream>>>(c.ly.cursor, (uint32_t)p.P, p.B, p.cap, c.ly.vsize, c.ly.voff,
+                                                   c.bucket_sizes, c.ly.status);
+    return cudaGetLastError();
+}
+
 size_t route_smem_bytes(const Plan &pl) {
+    if (!pl.pairs) return route_keys_smem_bytes(pl);
     const uint32_t P = (uint32_t)pl.P;
     const bool l = pl.classify == BSPS_LEARNED;
-    if (pl.key_bytes == 8) {
-        if (l) return pl.pairs ? RouteSmemLayout<uint64_t, true, true>(P).total : RouteSmemLayout<uint64_t, false, true>(P).total;
-        return pl.pairs ? RouteSmemLayout<uint64_t, true>(P).total : RouteSmemLayout<uint64_t, false>(P).total;
-    }
-    if (l) return pl.pairs ? RouteSmemLayout<uint32_t, true, true>(P).total : RouteSmemLayout<uint32_t, false, true>(P).total;
-    return pl.pairs ? RouteSmemLayout<uint32_t, true>(P).total : RouteSmemLayout<uint32_t, false>(P).total;
+    if (pl.key_bytes == 8) return l ? RouteSmemLayout<uint64_t, true>(P).total : RouteSmemLayout<uint64_t>(P).total;
+    return l ? RouteSmemLayout<uint32_t, true>(P).total : RouteSmemLayout<uint32_t>(P).total;
 }
 
 } // namespace bsps

@@ -3,15 +3,17 @@
 // stable and every rank comes from one shared-memory atomic.
 //
 // A cluster of CL CTAs (512 threads, two per SM) sorts one sub-bucket whose
-// keys lie in [lo, hi] (bounds from the splitters).  Each CTA copies its share
-// into shared memory with 16-byte loads, counts its keys per split bin (the
-// top bits of key - lo), the counts are exchanged through distributed shared
-// memory, and every key is stored into the shared memory of the CTA that owns
-// its bin; bins holding one distinct key are written out directly.  Each CTA
-// then counting-sorts what it received on up to kCountBits further bits and
-// finishes the (short) count bins by insertion.  A split bin too large for one
-// CTA makes the cluster give the sub-bucket back (returns false) to the
-// stable cluster sort of segsort.cuh.
+// keys lie in [lo, hi] (bounds from the splitters).  Each CTA loads its share
+// into registers with 16-byte loads and ranks its keys per split bin (the top
+// bits of key - lo), grouping them by bin in a local stage buffer.  The bin
+// counts are read across the cluster through distributed shared memory; bins
+// holding one distinct key are written out directly, every other bin is given
+// to one CTA, and each CTA copies its stage, bin run by bin run, into the
+// owners' receive buffers.  Each CTA then counting-sorts what it received on
+// up to kCountBits further bits (about one key per count bin) and places the
+// keys that share a count bin by comparison.  A bin too large for one CTA, or
+// count bins longer than kBinMax, make the cluster give the sub-bucket back
+// (returns false) to the stable cluster sort of segsort.cuh.
 #pragma once
 
 #include "radix.cuh"
@@ -21,33 +23,40 @@ namespace bsps {
 template <typename K, int CL, int ITEMS>
 struct SegSortKeys {
     static constexpr int T = 512;
-    static constexpr int CAP = T * ITEMS;            // keys one CTA holds
-    static constexpr int SB = 8, R = 1 << SB;        // split bins
-    static constexpr int kCountBits = 12, kCountBins = 1 << kCountBits;
+    static constexpr int V = 16 / (int)sizeof(K);     // keys per 16-byte load
+    static constexpr int CAP = T * ITEMS;             // keys one CTA holds
+    static constexpr int SB = 8, R = 1 << SB;         // split bins
+    static constexpr int kCountBits = 13, kCountBins = 1 << kCountBits;
+    static constexpr uint32_t kBinMax = 64;           // longest count bin ordered by comparison
+    static_assert(ITEMS % V == 0, "whole 16-byte loads per thread");
+    static_assert(kCountBins % (4 * T) == 0, "whole 16-byte groups of count bins per thread in the scan");
 
     struct Smem {
-        uint32_t tot[R];     // keys of the bin in the sub-bucket (local counts until the exchange)
+        uint32_t cnt[R];     // my keys per split bin (read by the other CTAs)
+        K bmin[R], bmax[R];  // my smallest / largest key per split bin (read by the others)
+        uint32_t lbase[R];   // start of the bin in my stage
+        uint32_t start[R];   // first output position of the bin
         uint32_t pre[R];     // keys of the bin held by lower-ranked CTAs
-        uint32_t start[R];   // first sorted position of the bin
-        uint32_t nfs[R];     // start among non-flat bins
-        uint32_t lstart[R];  // start of the bin in its owner's buffer
-        int32_t owner[R];    // -1: flat bin
-        K bmin[R], bmax[R];
-        uint32_t chist[kCountBins + 1];
-        uint32_t recv[8], own_base[8];
+        uint32_t dst[R];     // start of the bin in its owner's receive buffer
+        int32_t owner[R];    // -1: bin with one distinct key (or none)
+        uint32_t recv[8], own_base[8], ofirst[8], olast[8];
         uint32_t tmp[40];
-        int32_t bail;
     };
     static constexpr size_t smem_bytes() {
-        return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)CAP * sizeof(K) + (size_t)CAP * 2 + 64;
+        return ((sizeof(Smem) + 15) & ~size_t(15)) + 2 * (size_t)CAP * sizeof(K);
     }
+    // the count histogram lives in the receive buffer, which is free by then
+    static_assert((size_t)(kCountBins + 4) * 4 <= (size_t)CAP * sizeof(K), "count bins fit the buffer");
+
     // bin of key k: (k - lo) >> shift, clamped to maxb so that a key outside
     // [lo, hi] can never index past a table
     __device__ static uint32_t bin(K k, K lo, int shift, uint32_t maxb) {
         const K d = (K)(k - lo) >> shift;
         return d < (K)maxb ? (uint32_t)d : maxb;
     }
-    // item i of a thread: slot i*T + tid (item-major; layout is free here)
+    // register i of a thread holds local key (i / V * T + tid) * V + i % V
+    __device__ static int lidx(int i) { return ((i / V) * T + (int)threadIdx.x) * V + i % V; }
+    // ... or, for keys taken from shared memory, key i * T + tid
     __device__ static int slot(int i) { return i * T + (int)threadIdx.x; }
 
     __device__ static void atomic_min_max(K *mn, K *mx, K v) {
@@ -60,221 +69,273 @@ struct SegSortKeys {
         }
     }
 
-    // Copy n keys from global to shared memory (16-byte loads where aligned).
-    __device__ static void load(K *dst, const K *__restrict__ src, int n) {
-        constexpr int V = 16 / sizeof(K);
-        const uintptr_t a = (uintptr_t)src;
-        int head = (int)(((16 - (a & 15)) & 15) / sizeof(K));
-        if (head > n) head = n;
-        if ((a % sizeof(K)) != 0) head = n;  // not even key-aligned: scalar copy
-        for (int j = threadIdx.x; j < head; j += T) dst[j] = src[j];
-        const int nv = (n - head) / V;
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
-        for (int j = threadIdx.x; j < nv; j += T) {
-            const uint4 w = __ldg(s4 + j);
-            K *d = dst + head + j * V;
-            if constexpr (sizeof(K) == 4) {
-                d[0] = w.x; d[1] = w.y; d[2] = w.z; d[3] = w.w;
-            } else {
-                d[0] = ((uint64_t)w.y << 32) | w.x;
-                d[1] = ((uint64_t)w.w << 32) | w.z;
-            }
-        }
-        for (int j = head + nv * V + threadIdx.x; j < n; j += T) dst[j] = src[j];
-    }
-
-    // Sort buf[0..cnt) (keys in [lo, lo + 2^bits)) in place on this CTA: one
-    // counting pass (ranks from atomics, keys held in registers across the
-    // scatter), then insertion inside every count bin.
-    static constexpr uint32_t kBinMax = 64;  // longest count bin finished by insertion
-
-    __device__ static bool count_sort(Smem &sm, K *buf, int cnt, K lo, int bits) {
-        const int nbb = bits < kCountBits ? bits : kCountBits;
-        const int shift = bits - nbb;
-        const int nb = 1 << nbb;
-        for (int b = threadIdx.x; b <= nb; b += T) sm.chist[b] = 0;
-        __syncthreads();
-        K k[ITEMS];
-        uint32_t r[ITEMS];
+    // n keys from global memory (16-byte aligned; reading up to the next
+    // multiple of V keys stays inside the caller's region) into registers
+    __device__ static void load(K (&k)[ITEMS], const K *__restrict__ src, int n) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const int j = slot(i);
-            if (j < cnt) {
-                k[i] = buf[j];
-                r[i] = atomicAdd(&sm.chist[bin(k[i], lo, shift, nb - 1)], 1u);
-            }
-        }
-        if (threadIdx.x == 0) sm.bail = 0;
-        __syncthreads();
-        if (shift > 0) {
-            uint32_t longest = 0;
-            for (int b = threadIdx.x; b < nb; b += T) longest = max(longest, sm.chist[b]);
-            if (longest > kBinMax) sm.bail = 1;
-        }
-        __syncthreads();
-        if (sm.bail) return false;  // uniform in the CTA
-        block_excl_scan_smem<T>(sm.chist, nb, sm.tmp);
-        if (threadIdx.x == 0) sm.chist[nb] = (uint32_t)cnt;
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (slot(i) < cnt) buf[sm.chist[bin(k[i], lo, shift, nb - 1)] + r[i]] = k[i];
-        __syncthreads();
-        if (shift > 0) {
-            for (int b = threadIdx.x; b < nb; b += T) {
-                const int b0 = (int)sm.chist[b], b1 = (int)sm.chist[b + 1];
-                for (int x = b0 + 1; x < b1; ++x) {
-                    const K v = buf[x];
-                    int y = x - 1;
-                    while (y >= b0 && buf[y] > v) {
-                        buf[y + 1] = buf[y];
-                        --y;
-                    }
-                    buf[y + 1] = v;
+        for (int j = 0; j < ITEMS / V; ++j) {
+            const int q = j * T + (int)threadIdx.x;
+            if (q * V < n) {
+                const uint4 w = __ldg(s4 + q);
+                if constexpr (sizeof(K) == 4) {
+                    k[j * V + 0] = w.x; k[j * V + 1] = w.y; k[j * V + 2] = w.z; k[j * V + 3] = w.w;
+                } else {
+                    k[j * V + 0] = ((uint64_t)w.y << 32) | w.x;
+                    k[j * V + 1] = ((uint64_t)w.w << 32) | w.z;
                 }
             }
-            __syncthreads();
         }
+    }
+
+    // Exclusive scan of h[0..nb) (nb <= kCountBins) in place, h[nb] = total.
+    // With check, returns false (uniformly) if a bin holds more than kBinMax.
+    __device__ static bool scan_bins(uint32_t *h, int nb, uint32_t *tmp, bool check) {
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        constexpr int W = T / 32;
+        const int per = (nb + T - 1) / T;
+        const int b0 = tid * per;
+        const bool vec = (per & 3) == 0;
+        uint32_t s = 0, mx = 0;
+        if (vec) {
+            for (int q = 0; q < per; q += 4) {
+                const uint4 a = *reinterpret_cast<const uint4 *>(h + b0 + q);
+                s += a.x + a.y + a.z + a.w;
+                mx = max(max(mx, max(a.x, a.y)), max(a.z, a.w));
+            }
+        } else {
+            for (int q = 0; q < per && b0 + q < nb; ++q) {
+                s += h[b0 + q];
+                mx = max(mx, h[b0 + q]);
+            }
+        }
+        uint32_t wtot;
+        const uint32_t wex = warp_excl_scan(s, &wtot);
+        if (lane == 31) tmp[warp] = wtot;
+        if (__syncthreads_or(check && mx > kBinMax)) return false;
+        if (warp == 0) {
+            const uint32_t y = lane < W ? tmp[lane] : 0u;
+            uint32_t t;
+            const uint32_t ye = warp_excl_scan(y, &t);
+            if (lane < W) tmp[lane] = ye;
+            if (lane == 0) tmp[W] = t;
+        }
+        __syncthreads();
+        uint32_t run = tmp[warp] + wex;
+        if (vec) {
+            for (int q = 0; q < per; q += 4) {
+                uint4 a = *reinterpret_cast<const uint4 *>(h + b0 + q);
+                const uint4 o = make_uint4(run, run + a.x, run + a.x + a.y, run + a.x + a.y + a.z);
+                run += a.x + a.y + a.z + a.w;
+                *reinterpret_cast<uint4 *>(h + b0 + q) = o;
+            }
+        } else {
+            for (int q = 0; q < per && b0 + q < nb; ++q) {
+                const uint32_t x = h[b0 + q];
+                h[b0 + q] = run;
+                run += x;
+            }
+        }
+        if (tid == 0) h[nb] = tmp[W];
+        __syncthreads();
         return true;
     }
 
-    // Returns false when the sub-bucket does not fit this cluster or a CTA's
-    // count bins are too long; the caller then hands it to the stable sort,
-    // which rewrites every position (keys already emitted are rewritten with
-    // the same values).
+    // Sort the keys held in registers (valid where valid(i); all in
+    // [lo, lo + 2^bits)) into out[0..n): one counting pass on the top
+    // kCountBits bits, then the place of each key that shares its count bin
+    // by comparison.  chist is free shared memory of kCountBins + 4 words.
+    template <typename Valid>
+    __device__ static bool count_sort(Smem &sm, const K (&k)[ITEMS], Valid valid, K lo, int bits, K *out,
+                                      uint32_t *chist) {
+        const int nbb = bits < kCountBits ? bits : kCountBits;
+        const int shift = bits - nbb;
+        const int nb = 1 << nbb;
+        __syncthreads();  // chist may still be read by the caller
+        for (int b = threadIdx.x; b < nb; b += T) chist[b] = 0;
+        __syncthreads();
+        uint32_t r[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i)) r[i] = atomicAdd(&chist[bin(k[i], lo, shift, nb - 1)], 1u);
+        __syncthreads();
+        if (!scan_bins(chist, nb, sm.tmp, shift > 0)) return false;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i)) {
+                r[i] += chist[bin(k[i], lo, shift, nb - 1)];
+                out[r[i]] = k[i];
+            }
+        if (shift == 0) {  // one value per count bin: placed
+            __syncthreads();
+            return true;
+        }
+        __syncthreads();
+        // place = bin start + keys of the bin below k + equal keys stored before it
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i)) {
+                const uint32_t bb = bin(k[i], lo, shift, nb - 1);
+                const uint32_t b0 = chist[bb], b1 = chist[bb + 1], self = r[i];
+                if (b1 - b0 > 1) {
+                    uint32_t pos = b0;
+                    for (uint32_t y = b0; y < b1; ++y) {
+                        const K x = out[y];
+                        pos += (x < k[i]) | ((x == k[i]) & (y < self));
+                    }
+                    r[i] = pos;
+                }
+            }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i)) out[r[i]] = k[i];
+        __syncthreads();
+        return true;
+    }
+
+    // Sorts the cnt keys at gsrc (bounds lo <= key <= hi) and calls
+    // emit(position, key) for each.  Returns false when the sub-bucket does not
+    // fit this cluster or its bins are too uneven; the caller then hands it to
+    // the stable sort, which rewrites every position (keys already emitted are
+    // rewritten with the same values).  smem holds Smem, then the stage and the
+    // receive buffer (CAP keys each).
     template <typename Emit>
-    __device__ static bool run(Smem &sm, K *buf, uint16_t *rk, const K *__restrict__ gsrc, int64_t cnt, K lo, K hi,
-                               Emit emit) {
+    __device__ static bool run(unsigned char *smem, const K *__restrict__ gsrc, int64_t cnt, K lo, K hi, Emit emit) {
+        Smem &sm = *reinterpret_cast<Smem *>(smem);
+        K *stage = reinterpret_cast<K *>(smem + ((sizeof(Smem) + 15) & ~size_t(15)));
+        K *buf = stage + CAP;
         auto cluster = cg::this_cluster();
         const int c = CL > 1 ? (int)cluster.block_rank() : 0;
-        const int64_t share = ((cnt + CL - 1) / CL + 3) & ~int64_t(3);
+        const int64_t share = ((cnt + CL - 1) / CL + V - 1) / V * V;
         if (share > CAP) return false;
         const int64_t e0 = (int64_t)c * share;
         const int mycnt = (int)imax64(0, imin64(share, cnt - e0));
         const int bits = bit_length<K>(hi - lo);
-        load(buf, gsrc + e0, mycnt);
-        __syncthreads();
+        K k[ITEMS];
+        load(k, gsrc + e0, mycnt);
+        auto mine = [&](int i) { return lidx(i) < mycnt; };
         if (bits == 0) {  // one distinct key
-            for (int j = threadIdx.x; j < mycnt; j += T) emit((uint32_t)(e0 + j), buf[j]);
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (mine(i)) emit((uint32_t)(e0 + lidx(i)), k[i]);
             return true;
         }
         if constexpr (CL == 1) {
-            if (!count_sort(sm, buf, mycnt, lo, bits)) return false;
-            for (int j = threadIdx.x; j < mycnt; j += T) emit((uint32_t)j, buf[j]);
+            if (!count_sort(sm, k, mine, lo, bits, stage, reinterpret_cast<uint32_t *>(buf))) return false;
+            for (int j = threadIdx.x; j < mycnt; j += T) emit((uint32_t)j, stage[j]);
             return true;
         } else {
             const int sb = bits < SB ? bits : SB;
             const int shift = bits - sb;
             const int nbins = 1 << sb;
-            for (int b = threadIdx.x; b < R; b += T) {
-                sm.tot[b] = 0;
-                sm.bmin[b] = all_ones<K>();
-                sm.bmax[b] = 0;
+            const int tid = threadIdx.x;
+            if (tid < R) {
+                sm.cnt[tid] = 0;
+                sm.bmin[tid] = all_ones<K>();
+                sm.bmax[tid] = 0;
+            }
+            if (tid < 8) {
+                sm.recv[tid] = 0;
+                sm.own_base[tid] = 0xffffffffu;
+                sm.ofirst[tid] = 0xffffffffu;
+                sm.olast[tid] = 0;
             }
             __syncthreads();
-            K k[ITEMS];
+            uint32_t r[ITEMS];
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const int j = slot(i);
-                if (j < mycnt) {
-                    k[i] = buf[j];
+            for (int i = 0; i < ITEMS; ++i)
+                if (mine(i)) {
                     const uint32_t d = bin(k[i], lo, shift, nbins - 1);
-                    rk[j] = (uint16_t)atomicAdd(&sm.tot[d], 1u);
+                    r[i] = atomicAdd(&sm.cnt[d], 1u);
                     atomic_min_max(&sm.bmin[d], &sm.bmax[d], k[i]);
                 }
-            }
+            __syncthreads();
+            if (tid < R) sm.lbase[tid] = sm.cnt[tid];
+            __syncthreads();
+            digit_excl_scan<T, R>(sm.lbase, sm.tmp);
+            // group my keys by bin in the stage
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (mine(i)) stage[sm.lbase[bin(k[i], lo, shift, nbins - 1)] + r[i]] = k[i];
             cluster.sync();
-            // every CTA derives the same global bin layout
+            // every CTA derives the same global bin layout from all counts
             uint32_t tot = 0, pre = 0;
             K gmin = all_ones<K>(), gmax = 0;
-            const int b = threadIdx.x;
-            if (b < nbins) {
+            if (tid < nbins) {
 #pragma unroll
-                for (int r = 0; r < CL; ++r) {
-                    const uint32_t t = *cluster.map_shared_rank(&sm.tot[b], r);
-                    const K x = *cluster.map_shared_rank(&sm.bmin[b], r);
-                    const K y = *cluster.map_shared_rank(&sm.bmax[b], r);
-                    pre += r < c ? t : 0;
+                for (int q = 0; q < CL; ++q) {
+                    const uint32_t t = *cluster.map_shared_rank(&sm.cnt[tid], q);
+                    const K x = *cluster.map_shared_rank(&sm.bmin[tid], q);
+                    const K y = *cluster.map_shared_rank(&sm.bmax[tid], q);
+                    pre += q < c ? t : 0u;
                     tot += t;
                     gmin = x < gmin ? x : gmin;
                     gmax = y > gmax ? y : gmax;
                 }
             }
-            // all remote reads are done and every key sits in registers: from
-            // here on a CTA's buffer may be written by the others
-            cluster.sync();
             const bool flat = tot == 0 || gmin == gmax;
-            if (b < R) {
-                sm.tot[b] = tot;
-                sm.pre[b] = pre;
-                sm.start[b] = tot;
-                sm.nfs[b] = flat ? 0 : tot;
-            }
-            if (threadIdx.x < 8) {
-                sm.recv[threadIdx.x] = 0;
-                sm.own_base[threadIdx.x] = 0xffffffffu;
+            if (tid < R) {
+                sm.pre[tid] = pre;
+                sm.start[tid] = tot;
+                sm.dst[tid] = flat ? 0u : tot;
             }
             __syncthreads();
+            if (tid == R - 1) sm.tmp[39] = sm.dst[R - 1];
             digit_excl_scan<T, R>(sm.start, sm.tmp);
-            if (threadIdx.x == R - 1) sm.tmp[39] = sm.nfs[R - 1];
-            __syncthreads();
             const uint32_t last_nf = sm.tmp[39];
-            digit_excl_scan<T, R>(sm.nfs, sm.tmp);
-            const uint32_t total_nf = sm.nfs[R - 1] + last_nf;
+            digit_excl_scan<T, R>(sm.dst, sm.tmp);
+            const uint32_t total_nf = sm.dst[R - 1] + last_nf;
             const uint32_t target = (total_nf + CL - 1) / CL;
-            if (b < R) {
-                if (!flat && tot > 0) {
-                    const int t = target ? min(CL - 1, (int)(sm.nfs[b] / target)) : 0;
-                    sm.owner[b] = t;
+            if (tid < R) {
+                int t = -1;
+                if (!flat) {
+                    t = target ? min(CL - 1, (int)(sm.dst[tid] / target)) : 0;
                     atomicAdd(&sm.recv[t], tot);
-                    atomicMin(&sm.own_base[t], sm.nfs[b]);
-                } else {
-                    sm.owner[b] = -1;
+                    atomicMin(&sm.own_base[t], sm.dst[tid]);
+                    atomicMin(&sm.ofirst[t], (uint32_t)tid);
+                    atomicMax(&sm.olast[t], (uint32_t)tid);
                 }
+                sm.owner[tid] = t;
             }
             __syncthreads();
-            if (b < R) sm.lstart[b] = sm.owner[b] >= 0 ? sm.nfs[b] - sm.own_base[sm.owner[b]] : 0;
-            if (threadIdx.x == 0) {
-                int bail = 0;
-                for (int t = 0; t < CL; ++t) bail |= sm.recv[t] > (uint32_t)CAP;
-                sm.bail = bail;
-            }
-            __syncthreads();
-            if (sm.bail) return false;  // uniform; nobody touches another CTA's memory any more
-            // exchange: every key to its bin's owner, flat bins straight out
+            if (tid < R && sm.owner[tid] >= 0) sm.dst[tid] -= sm.own_base[sm.owner[tid]];
+            bool bail = false;
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const int j = slot(i);
-                if (j < mycnt) {
-                    const uint32_t d = bin(k[i], lo, shift, nbins - 1);
-                    const int t = sm.owner[d];
-                    if (t < 0) {
-                        emit(sm.start[d] + sm.pre[d] + rk[j], k[i]);
-                    } else {
-                        K *rb = cluster.map_shared_rank(buf, t);
-                        rb[sm.lstart[d] + sm.pre[d] + rk[j]] = k[i];
-                    }
-                }
+            for (int q = 0; q < CL; ++q) bail |= sm.recv[q] > (uint32_t)CAP;
+            if (bail) {  // uniform: every CTA saw the same counts
+                cluster.sync();  // nobody reads this CTA's counts any more
+                return false;
+            }
+            __syncthreads();
+            // exchange: stage runs to their owners, one-key bins straight out
+            for (int j = tid; j < mycnt; j += T) {
+                const K x = stage[j];
+                const uint32_t d = bin(x, lo, shift, nbins - 1);
+                const uint32_t at = sm.pre[d] + ((uint32_t)j - sm.lbase[d]);
+                const int t = sm.owner[d];
+                if (t < 0) emit(sm.start[d] + at, x);
+                else cluster.map_shared_rank(buf, t)[sm.dst[d] + at] = x;
             }
             cluster.sync();
             const int got = (int)sm.recv[c];
             if (got == 0) return true;
-            // received keys lie in the owned bins
-            int first = R, last = -1;
-            for (int bb = 0; bb < nbins; ++bb)
-                if (sm.owner[bb] == c) {
-                    first = bb < first ? bb : first;
-                    last = bb;
-                }
+            // received keys lie in the owned bins [ofirst, olast]
+            const uint32_t first = sm.ofirst[c], last = sm.olast[c];
             const K llo = lo + ((K)first << shift);
-            const K lhi = last == nbins - 1 ? hi : lo + ((K)(last + 1) << shift) - 1;
-            const int lbits = bit_length<K>(lhi - llo);
+            const K lhi = last == (uint32_t)nbins - 1 ? hi : lo + ((K)(last + 1) << shift) - 1;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (slot(i) < got) k[i] = buf[slot(i)];
+            auto received = [&](int i) { return slot(i) < got; };
             // a CTA that cannot finish its bins gives the sub-bucket back; what
             // the others emit is rewritten, identically, by the stable sort
-            if (!count_sort(sm, buf, got, llo, lbits)) return false;
-            for (int j = threadIdx.x; j < got; j += T) {
-                const K x = buf[j];
+            if (!count_sort(sm, k, received, llo, bit_length<K>(lhi - llo), stage, reinterpret_cast<uint32_t *>(buf)))
+                return false;
+            for (int j = tid; j < got; j += T) {
+                const K x = stage[j];
                 const uint32_t d = bin(x, lo, shift, nbins - 1);
-                emit(sm.start[d] + (uint32_t)j - sm.lstart[d], x);
+                emit(sm.start[d] + ((uint32_t)j - sm.dst[d]), x);
             }
             return true;
         }
