@@ -237,6 +237,83 @@ int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y
 int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, int64_t n, int32_t dtype,
                            const bsps_params *prm, int64_t *d_bucket_sizes, void *stream);
 
+/*
+ * ---- Batched sorting: many independent keys-only sorts in one call --------
+ *
+ * No counterpart in the paper: it applies the paper's sort (Fig. 2 / Fig. 3)
+ * to many inputs of uneven sizes at once.  Instance i is the key range
+ * [h_offsets[i], h_offsets[i+1]) of d_keys_in; it is sorted into the same
+ * range of d_keys_out exactly as bsps_sort_keys sorts it with the parameters
+ *   p        = t->p[c], c the instance's size class: sizes in (2^(c-1), 2^c]
+ *              (class 0: sizes 0 and 1);
+ *   s, runs, sampling, refine, capacity_pct  from *prm (s = 0: the paper's
+ *              default for that instance's size);
+ *   seed     = prm->seed + i;
+ *   classify = BSPS_LEARNED for sizes > 2^(t->learned_min_log2 - 1) when
+ *              t->learned_min_log2 > 0, else prm->classify.
+ * so its sorted keys and its p bucket sizes are those of that single call.
+ *
+ * Instances of class <= t->small_max_log2 (at most BSPS_BATCH_SMALL_MAX keys)
+ * with random oversampling, 32-bit keys, the tree classifier and a sample of
+ * at most BSPS_BATCH_SAMPLE_MAX records run the whole method on chip, one CTA
+ * per instance, in one persistent launch (sample, sample sort, splitters,
+ * classification, bucket histogram, routing into buckets and the final sort
+ * all in shared memory).  The others run the single-instance pipeline on
+ * t->lanes streams that fork from and join back into `stream`.  Unless
+ * `stream` is already being captured, the call records all of this into one
+ * CUDA graph; the instantiated graph is kept and relaunched by later calls
+ * with the same arguments (pointers, offsets, parameters, table).
+ *
+ * h_offsets: host array of num+1 nondecreasing key offsets, h_offsets[0] = 0.
+ * d_bucket_sizes: device int64 array (nullable) of the instances' bucket
+ *   sizes, instance i's p_i sizes starting at entry h_base[i] from
+ *   bsps_batch_bucket_base().
+ * Keys are 32- or 64-bit (the on-chip path takes 32-bit keys only).
+ * Errors: BSPS_ERR_INVALID_ARG (bad offsets, num < 0, in == out, bad table),
+ * BSPS_ERR_WORKSPACE_TOO_SMALL, BSPS_ERR_TOO_LARGE (an instance too large
+ * for bsps_sort_keys), BSPS_ERR_CUDA.  Device-side statuses of all instances
+ * (overflow, timeouts) are merged into the batch status that
+ * bsps_read_stats(d_ws, ...) reads.
+ */
+#define BSPS_BATCH_CLASSES 32
+#define BSPS_BATCH_SMALL_MAX 16384
+#define BSPS_BATCH_SAMPLE_MAX 8192
+typedef struct {
+    int32_t p[BSPS_BATCH_CLASSES]; /* buckets per size class (>= 1) */
+    int32_t small_max_log2;        /* classes up to this one run on chip (<= 14; -1: none) */
+    int32_t learned_min_log2;      /* classes from this one up use the learned classifier; 0: never */
+    int32_t lanes;                 /* concurrent streams for the other instances, 1..16 */
+    int32_t reserved;
+} bsps_tune;
+
+/* bsps_tune_default -- a table that needs no measurement. */
+int bsps_tune_default(bsps_tune *t);
+
+/* bsps_batch_bucket_base -- h_base[i] (num+1 entries, host) = first entry of
+ * instance i in the flat bucket-size array; h_base[num] = its length. */
+int bsps_batch_bucket_base(const int64_t *h_offsets, int32_t num, const bsps_tune *t, int64_t *h_base);
+
+/* bsps_batch_workspace_size -- device workspace bytes for bsps_sort_batched. */
+int bsps_batch_workspace_size(const int64_t *h_offsets, int32_t num, int32_t dtype, const bsps_params *prm,
+                              const bsps_tune *t, size_t *bytes);
+
+int bsps_sort_batched(const void *d_keys_in, void *d_keys_out, const int64_t *h_offsets, int32_t num,
+                      int32_t dtype, const bsps_params *prm, const bsps_tune *t, int64_t *d_bucket_sizes,
+                      void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * bsps_autotune_batched -- fills *t by measurement on the current device.
+ * For every size class from 8 to max_log2 it sorts seeded uniform keys of
+ * that size with each candidate p (on chip: 1, 2, 4, 8, 16; pipeline:
+ * 16 ... 4096) and keeps the fastest (CUDA events, median of three runs);
+ * small_max_log2 is the largest class for which the on-chip form beat the
+ * pipeline.  lanes and learned_min_log2 are taken from *t as given.
+ * d_ws: at least bsps_autotune_workspace_size() bytes.  Synchronizes stream.
+ */
+int bsps_autotune_workspace_size(int32_t dtype, const bsps_params *prm, int32_t max_log2, size_t *bytes);
+int bsps_autotune_batched(int32_t dtype, const bsps_params *prm, int32_t max_log2, bsps_tune *t, void *d_ws,
+                          size_t ws_bytes, void *stream);
+
 /* bsps_strerror -- static text for a status code. */
 const char *bsps_strerror(int status);
 

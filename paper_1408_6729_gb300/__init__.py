@@ -27,7 +27,12 @@ BSPS_ERR_TOO_LARGE = -7
 
 EXPORTS = ["bsps_get_plan", "bsps_workspace_size", "bsps_sort_keys", "bsps_sort_pairs",
            "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad",
-           "bsps_sort_keys_noalloc", "bsps_strerror"]
+           "bsps_sort_keys_noalloc", "bsps_tune_default", "bsps_batch_bucket_base",
+           "bsps_batch_workspace_size", "bsps_sort_batched", "bsps_autotune_workspace_size",
+           "bsps_autotune_batched", "bsps_strerror"]
+BSPS_BATCH_CLASSES = 32
+BSPS_BATCH_SMALL_MAX = 16384
+BSPS_BATCH_SAMPLE_MAX = 8192
 BSPS_NOALLOC_SCRATCH_BYTES = 64 << 20
 MLP_PARAMS = 1153
 
@@ -61,6 +66,11 @@ class bsps_stats(ctypes.Structure):
 BSPS_PHASES = 6
 
 
+class bsps_tune(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32 * 32), ("small_max_log2", ctypes.c_int32),
+                ("learned_min_log2", ctypes.c_int32), ("lanes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class bsps_debug(ctypes.Structure):
     _fields_ = [("sample", ctypes.c_void_p), ("splitters", ctypes.c_void_p),
                 ("bucket_of", ctypes.c_void_p), ("pad_sizes", ctypes.c_void_p),
@@ -92,6 +102,13 @@ def load(path: str = LIB_PATH):
     lib.bsps_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
     lib.bsps_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, SZ, P]
     lib.bsps_sort_keys_noalloc.argtypes = [P, P, I64, I32, PP, P, P]
+    PT, PI64 = ctypes.POINTER(bsps_tune), ctypes.POINTER(ctypes.c_int64)
+    lib.bsps_tune_default.argtypes = [PT]
+    lib.bsps_batch_bucket_base.argtypes = [PI64, I32, PT, PI64]
+    lib.bsps_batch_workspace_size.argtypes = [PI64, I32, I32, PP, PT, ctypes.POINTER(SZ)]
+    lib.bsps_sort_batched.argtypes = [P, P, PI64, I32, I32, PP, PT, P, P, SZ, P]
+    lib.bsps_autotune_workspace_size.argtypes = [I32, PP, I32, ctypes.POINTER(SZ)]
+    lib.bsps_autotune_batched.argtypes = [I32, PP, I32, PT, P, SZ, P]
     lib.bsps_strerror.argtypes = [ctypes.c_int]
     lib.bsps_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -207,6 +224,61 @@ def bsps_mlp_workspace_size(m) -> int:
 def bsps_mlp_loss_grad(params, x, y, m, grad, loss, workspace, stream=None) -> int:
     return load().bsps_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), int(m), _ptr(grad), _ptr(loss),
                                      _ptr(workspace), _nbytes(workspace), _stream(stream))
+
+
+def _offsets(offsets):
+    """Host int64 offsets (a sequence or numpy array) as a ctypes array."""
+    vals = [int(v) for v in offsets]
+    return (ctypes.c_int64 * max(1, len(vals)))(*vals), len(vals) - 1
+
+
+def bsps_tune_default() -> bsps_tune:
+    t = bsps_tune()
+    rc = load().bsps_tune_default(ctypes.byref(t))
+    if rc:
+        raise ValueError(f"bsps_tune_default: {bsps_strerror(rc)} ({rc})")
+    return t
+
+
+def bsps_batch_bucket_base(offsets, tune) -> list:
+    arr, num = _offsets(offsets)
+    base = (ctypes.c_int64 * (num + 1))()
+    rc = load().bsps_batch_bucket_base(arr, num, ctypes.byref(tune), base)
+    if rc:
+        raise ValueError(f"bsps_batch_bucket_base: {bsps_strerror(rc)} ({rc})")
+    return list(base)
+
+
+def bsps_batch_workspace_size(offsets, dtype, params, tune) -> int:
+    arr, num = _offsets(offsets)
+    out = ctypes.c_size_t()
+    rc = load().bsps_batch_workspace_size(arr, num, int(dtype), ctypes.byref(params), ctypes.byref(tune),
+                                          ctypes.byref(out))
+    if rc:
+        raise ValueError(f"bsps_batch_workspace_size: {bsps_strerror(rc)} ({rc})")
+    return out.value
+
+
+def bsps_sort_batched(keys_in, keys_out, offsets, dtype, params, tune, bucket_sizes, workspace,
+                      stream=None) -> int:
+    """offsets: host sequence of num+1 key offsets (see include/bspsort.h)."""
+    arr, num = _offsets(offsets)
+    return load().bsps_sort_batched(_ptr(keys_in), _ptr(keys_out), arr, num, int(dtype), ctypes.byref(params),
+                                    ctypes.byref(tune), _ptr(bucket_sizes), _ptr(workspace), _nbytes(workspace),
+                                    _stream(stream))
+
+
+def bsps_autotune_workspace_size(dtype, params, max_log2) -> int:
+    out = ctypes.c_size_t()
+    rc = load().bsps_autotune_workspace_size(int(dtype), ctypes.byref(params), int(max_log2), ctypes.byref(out))
+    if rc:
+        raise ValueError(f"bsps_autotune_workspace_size: {bsps_strerror(rc)} ({rc})")
+    return out.value
+
+
+def bsps_autotune_batched(dtype, params, max_log2, tune, workspace, stream=None) -> int:
+    return load().bsps_autotune_batched(int(dtype), ctypes.byref(params), int(max_log2), ctypes.byref(tune),
+                                        _ptr(workspace), _nbytes(workspace), _stream(stream))
 
 
 def bsps_read_stats(workspace, stream=None) -> bsps_stats:
