@@ -45,6 +45,16 @@ WORKLOADS = {
     # quarter of the data (used for profiling captures)
     "uniform_2e26_int32_p1024_random": dict(n=1 << 26, p=1024, sampling=1, s=0, runs=0, pairs=False,
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    # learned classifier against the splitter tree: 2^28 float64 keys of an
+    # 8-component Gaussian mixture (Dirichlet(0.3) weights), p = 4096, s = 16
+    "gmm_2e28_f64_p4096_random_learned": dict(n=1 << 28, p=4096, sampling=1, s=16, runs=0, pairs=False,
+                                             dtype="f64", classify=1, compare="tree",
+                                             make=lambda n, p, seed: gen.gmm(n, seed=seed)),
+    # batched: 20,000 int32 instances, sizes log-uniform on [2^8, 2^22],
+    # alternately uniform [U] and Zipf(1.1) over 256 values; the first
+    # instances up to 2^28 keys in all, or all 20,000 (about 2^33 keys)
+    "batched_20000_int32_first_2e28": dict(kind="batched", count=20000, cap=1 << 28, p=0, sampling=1),
+    "batched_20000_int32_all": dict(kind="batched", count=20000, cap=None, p=0, sampling=1),
 }
 DEFAULT_WORKLOAD = "uniform_2e28_int32_p4096_random"
 METRIC = "keys/sec and % HBM roofline, 2^28 int32; learned/batched vs plain, bit-exact"
@@ -53,13 +63,19 @@ METRIC = "keys/sec and % HBM roofline, 2^28 int32; learned/batched vs plain, bit
 # routing pass reads every key and writes it once (8 B); the bucket sort reads
 # and writes every key once (8 B).  With 4-byte payloads both double.
 PHASES = ["sample", "sample_sort", "splitters", "route", "bucket_sort"]
-PHASE_KERNEL = {"route": "route_kernel", "bucket_sort": "bucket_sort_kernel"}
+PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "bucket_keys_kernel",
+                ("route", True): "route_kernel", ("bucket_sort", True): "bucket_sort_kernel"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
 # ncu capture (profiles/*.md), valid while the kernel source is unchanged.
 NCU_TRAFFIC = {}  # kernel -> (bytes per key, sha256 of the source file at capture)
-KERNEL_SOURCE = {"route_kernel": "paper_1408_6729_gb300/csrc/route.cu",
-                 "bucket_sort_kernel": "paper_1408_6729_gb300/csrc/bucket.cu"}
+KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
+                 "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
+                                       "paper_1408_6729_gb300/csrc/classify.cuh"],
+                 "bucket_sort_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
+                                        "paper_1408_6729_gb300/csrc/segsort.cuh"],
+                 "bucket_keys_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
+                                        "paper_1408_6729_gb300/csrc/segsort_keys.cuh"]}
 
 
 def peaks():
@@ -113,8 +129,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def source_hash(path):
-    return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+def source_hash(paths):
+    h = hashlib.sha256()
+    for path in paths:
+        h.update(open(os.path.join(ROOT, path), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def dist_setup(args):
@@ -204,11 +223,12 @@ def run_gpu(args, wl, name):
     barrier(pg)
     lib_build.build()  # no-op once built
     n, p = wl["n"], wl["p"]
-    code = bsps.BSPS_I32
+    f64 = wl.get("dtype") == "f64"
+    code = bsps.BSPS_F64 if f64 else bsps.BSPS_I32
     prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
-                           refine=args.refine)
+                           refine=args.refine, classify=wl.get("classify", 0))
     plan = bsps.bsps_get_plan(n, code, prm, wl["pairs"])
-    keys_h = wl["make"](n, p, 1 + rank)
+    keys_h = np.ascontiguousarray(wl["make"](n, p, 1 + rank))
     kin = torch.from_numpy(keys_h).to(dev)
     kout = torch.empty_like(kin)
     vin = vout = None
@@ -259,10 +279,16 @@ def run_gpu(args, wl, name):
     if st.status:
         raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
     # sanity of the last output (not part of the timed region)
-    ok = bool((kout[1:] >= kout[:-1]).all().item()) and int(kout.to(torch.int64).sum().item()) == int(
-        kin.to(torch.int64).sum().item())
+    if f64:
+        ok = bool((kout[1:] >= kout[:-1]).all().item()) and bool(torch.equal(torch.sort(kin).values, kout))
+    else:
+        ok = bool((kout[1:] >= kout[:-1]).all().item()) and int(kout.to(torch.int64).sum().item()) == int(
+            kin.to(torch.int64).sum().item())
     if not ok:
         raise RuntimeError("output is not a sorted permutation of the input")
+    compare = None
+    if wl.get("compare") == "tree":
+        compare = compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st, stream, elapsed_ms)
 
     # end to end through the C ABI with host buffers: H2D of the keys, the sort,
     # D2H of the sorted keys, every step
@@ -273,7 +299,34 @@ def run_gpu(args, wl, name):
     if rank != 0:
         return
     return report(args, wl, name, world, n, p, plan, st, per_step_of(phase_ms, args), elapsed_ms, e2e_ms,
-                  e2e_steps, total_launches, clk)
+                  e2e_steps, total_launches, clk, compare)
+
+
+def compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st_learned, stream, learned_ms):
+    """The same sort with the splitter tree: time, and identical output."""
+    import torch
+    prm = bsps.make_params(wl["p"], s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
+                           refine=args.refine, classify=0)
+    plan = bsps.bsps_get_plan(n, code, prm, False)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=kin.device)
+    out = torch.empty_like(kout)
+    sz = torch.empty_like(sizes)
+    for _ in range(args.warmup):
+        assert bsps.bsps_sort_keys(kin, out, n, code, prm, sz, ws) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        assert bsps.bsps_sort_keys(kin, out, n, code, prm, sz, ws) == 0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tree_ms = e0.elapsed_time(e1) / args.steps
+    same = bool(torch.equal(out.view(torch.int64) if code == bsps.BSPS_F64 else out,
+                            kout.view(torch.int64) if code == bsps.BSPS_F64 else kout)) and bool(torch.equal(sz, sizes))
+    return {"tree_ms_per_step": tree_ms, "learned_ms_per_step": learned_ms / args.steps,
+            "learned_vs_tree": tree_ms / (learned_ms / args.steps), "identical_output": same,
+            "mispredicted_frac": st_learned.mispredicted / n,
+            "correction_steps_per_key": st_learned.correction_steps / n}
 
 
 def per_step_of(phase_ms, args):
@@ -304,11 +357,13 @@ def run_e2e(args, stream, kin, kout, keys_h, step, pg, n):
     return e2e_ms, e2e_steps
 
 
-def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, e2e_steps, total_launches, clk):
+def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, e2e_steps, total_launches, clk,
+           compare=None):
     pk, pk_kind = peaks()
-    kb = 4 + (4 if wl["pairs"] else 0)
+    key_bytes = 8 if wl.get("dtype") == "f64" else 4
+    kb = key_bytes + (4 if wl["pairs"] else 0)
     dom = max(("route", "bucket_sort"), key=lambda k: per_step[k])
-    kern = PHASE_KERNEL[dom]
+    kern = PHASE_KERNEL[(dom, bool(wl["pairs"]))]
     alg_bytes = n * 2 * kb
     achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
     traffic = None
@@ -316,9 +371,10 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
         traffic = NCU_TRAFFIC[kern][0] * n
     ms_step = elapsed_ms / args.steps
     value = world * n / (ms_step * 1e-3)
-    b_alg = 4 * kb + plan.sample_size * (4 + 8) / n + (kb if wl["sampling"] == 0 else 0)
+    rec = 8 if key_bytes == 4 else 16
+    b_alg = 4 * kb + plan.sample_size * (key_bytes + 2 * rec) / n + (kb if wl["sampling"] == 0 else 0)
     cpu = None
-    if world == 1 and not args.no_baseline:
+    if world == 1 and not args.no_baseline and wl.get("dtype") != "f64":
         rate, ns, s_used, runs_used, t_used = oracle_rate(wl)
         cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"{ns} keys of the same generator, p={p}, s={s_used}, "
@@ -326,10 +382,11 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     line = {
         "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if key_bytes == 8 else "int32", "data": "synthetic",
         "config": {"workload": name, "n": n, "p": p, "sampling": "random" if wl["sampling"] else "regular",
                    "s": plan.s, "runs": plan.R, "sample_size": plan.sample_size, "pairs": wl["pairs"],
                    "refine": plan.refine, "bucket_cluster": plan.bucket_cluster,
+                   "classify": "learned" if wl.get("classify") else "tree",
                    "l2": "inputs (1 GiB) larger than L2 (126 MB); no flush",
                    "parallelism": f"independent sorts x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -340,11 +397,177 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
         "phases_ms": per_step,
         "cpu_baseline": cpu,
         "e2e": None if args.no_e2e else {"value": world * n * e2e_steps / (e2e_ms * 1e-3), "unit": "keys/s",
-                                         "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * 4},
+                                         "h2d_bytes_per_step": n * kb, "d2h_bytes_per_step": n * kb},
         "gpu_launches": total_launches,
         "clocks": clk.summary(),
         "stats": {"max_bucket": st.max_bucket, "max_vbucket": st.max_vbucket, "slow_buckets": st.slow_buckets,
                   "imbalance": st.max_bucket / (n / p) - 1},
+    }
+    if compare is not None:
+        line["learned_vs_tree"] = compare
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ batched arm
+
+def batched_keys(sizes, seed, dev):
+    """Instance i's keys: uniform [U] on [0, 2^31) for even i, Zipf(1.1) over
+    256 values for odd i, generated on the device in chunks."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    total = int(sizes.sum())
+    keys = torch.empty(total, dtype=torch.int32, device=dev)
+    table = torch.from_numpy(gen.zipf_values(256)).to(dev)
+    w = torch.arange(1, 257, dtype=torch.float64, device=dev) ** -1.1
+    cdf = torch.cumsum(w / w.sum(), 0)
+    cdf[-1] = 1.0
+    off, i0 = 0, 0
+    while i0 < len(sizes):
+        i1, m = i0, 0
+        while i1 < len(sizes) and (m == 0 or m + sizes[i1] <= (1 << 27)):
+            m += int(sizes[i1])
+            i1 += 1
+        parity = torch.from_numpy((np.arange(i0, i1) % 2).astype(np.int32)).to(dev)
+        odd = torch.repeat_interleave(parity, torch.from_numpy(sizes[i0:i1]).to(dev)).bool()
+        u = torch.randint(0, 2**31 - 1, (m,), generator=g, device=dev, dtype=torch.int64).to(torch.int32)
+        r = torch.searchsorted(cdf, torch.rand(m, generator=g, device=dev, dtype=torch.float64), right=True)
+        keys[off:off + m] = torch.where(odd, table[r.clamp_(max=255)], u)
+        off += m
+        i0 = i1
+    return keys
+
+
+def run_batched(args, wl, name):
+    import torch
+    import paper_1408_6729_gb300 as bsps
+    from paper_1408_6729_gb300 import build as lib_build
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        lib_build.build()
+    barrier(pg)
+    lib_build.build()
+    sizes = gen.batched_sizes(wl["count"], 8.0, 22.0, seed=1 + rank)
+    if wl["cap"] is not None:
+        keep = int(np.searchsorted(np.cumsum(sizes), wl["cap"], side="right"))
+        sizes = sizes[:max(1, keep)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    num, total = len(sizes), int(off[-1])
+    code = bsps.BSPS_I32
+    prm = bsps.make_params(1, sampling=wl["sampling"], seed=1 + rank)
+    stream = torch.cuda.current_stream()
+    # the autotuner's table (learned classifier from 2^18 keys up)
+    tune = bsps.bsps_tune_default()
+    tune.learned_min_log2 = 18
+    t0 = time.perf_counter()
+    tws = torch.empty(bsps.bsps_autotune_workspace_size(code, prm, 22), dtype=torch.uint8, device=dev)
+    rc = bsps.bsps_autotune_batched(code, prm, 22, tune, tws)
+    if rc:
+        raise RuntimeError(f"autotune: {bsps.bsps_strerror(rc)}")
+    del tws
+    tune_s = time.perf_counter() - t0
+    kin = batched_keys(sizes, 1 + rank, dev)
+    kout = torch.empty_like(kin)
+    base = bsps.bsps_batch_bucket_base(off, tune)
+    bsz = torch.empty(max(1, base[-1]), dtype=torch.int64, device=dev)
+    ws = torch.empty(bsps.bsps_batch_workspace_size(off, code, prm, tune), dtype=torch.uint8, device=dev)
+    offl = off.tolist()
+
+    def step():
+        rc = bsps.bsps_sort_batched(kin, kout, offl, code, prm, tune, bsz, ws)
+        if rc:
+            raise RuntimeError(bsps.bsps_strerror(rc))
+
+    t0 = time.perf_counter()
+    step()  # records the graph
+    torch.cuda.synchronize()
+    record_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        step()
+    st = bsps.bsps_read_stats(ws)
+    if st.status:
+        raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(pg)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    ms_step = max_over_ranks(pg, start.elapsed_time(end)) / args.steps
+    st = bsps.bsps_read_stats(ws)
+    if st.status:
+        raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
+
+    # the same instances as a loop of single-instance calls (identical output)
+    pws = torch.empty(max(bsps.bsps_workspace_size(int(sizes.max()), code,
+                                                   bsps.make_params(tune.p[c], sampling=wl["sampling"]))
+                          for c in range(8, 23)), dtype=torch.uint8, device=dev)
+    lout = torch.empty_like(kin)
+    lsz = torch.empty_like(bsz)
+    params = []
+    for i in range(num):
+        n = int(sizes[i])
+        c = 0
+        while (1 << c) < n:
+            c += 1
+        c = min(c, 31)
+        q = bsps.make_params(tune.p[c], sampling=wl["sampling"], seed=prm.seed + i,
+                             classify=1 if (tune.learned_min_log2 > 0 and c >= tune.learned_min_log2) else 0)
+        params.append(q)
+        need = bsps.bsps_workspace_size(n, code, q)
+        if need > pws.numel():
+            pws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def loop():
+        for i in range(num):
+            a, b = offl[i], offl[i + 1]
+            rc = bsps.bsps_sort_keys(kin[a:] if b > a else None, lout[a:] if b > a else None, b - a, code,
+                                     params[i], lsz[base[i]:], pws)
+            if rc:
+                raise RuntimeError(bsps.bsps_strerror(rc))
+
+    loop()
+    torch.cuda.synchronize()
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    l0.record(stream)
+    loop()
+    l1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = l0.elapsed_time(l1)
+    identical = bool(torch.equal(lout, kout)) and bool(torch.equal(lsz, bsz))
+    if not identical:
+        raise RuntimeError("batched output differs from the loop of single calls")
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    value = world * total / (ms_step * 1e-3)
+    alg = 16.0 * total
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": name, "instances": num, "keys": total, "sizes": "log-uniform [2^8, 2^22]",
+                   "mix": "uniform / Zipf(1.1) alternating", "sampling": "random",
+                   "on_chip_max_log2": tune.small_max_log2, "learned_min_log2": tune.learned_min_log2,
+                   "lanes": tune.lanes, "p_by_class": {c: tune.p[c] for c in range(8, 23)},
+                   "l2": "inputs larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "achieved": alg / (ms_step * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": alg / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "whole batched call (16 B/key: route and bucket sort read and write each key)",
+                     "peak_source": f"{pk_kind} hbm_gbs"},
+        "batched_vs_plain_loop": {"loop_ms": loop_ms, "batched_ms": ms_step, "speedup": loop_ms / ms_step,
+                                  "identical_output": identical},
+        "autotune_s": tune_s, "graph_record_s": record_s,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+        "stats": {"max_bucket": st.max_bucket, "slow_buckets": st.slow_buckets, "mispredicted": st.mispredicted},
     }
     print(json.dumps(line), flush=True)
 
@@ -362,7 +585,12 @@ def main():
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
+        if wl.get("kind") == "batched":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single sorts only"}))
+            return
         run_reference(args, wl, args.workload)
+    elif wl.get("kind") == "batched":
+        run_batched(args, wl, args.workload)
     else:
         run_gpu(args, wl, args.workload)
 

@@ -11,7 +11,9 @@ against the true splitters corrects every prediction, so buckets are exactly
 
 Network: x -> h1 = relu(W1 x + b1) (32) -> h2 = relu(W2 h1 + b2) (32)
 -> y = w3 . h2 + b3.  Loss: mean squared error against the empirical CDF of
-the sorted sample, y_i = (i + 1/2) / S.  Parameters are packed in one vector
+the sorted sample, y_i = (i + 1/2) / S.  Training starts from the
+piecewise-linear interpolant of the training points (spline_start) and takes
+full-batch gradient steps on the output layer (head_step).  Parameters are packed in one vector
 in the order W1 (32), b1 (32), W2 (32x32, row-major, W2[i, j] multiplies
 h1[j] into unit i), b2 (32), w3 (32), b3 (1): 1153 values.
 """
@@ -66,13 +68,42 @@ def loss_and_grad(theta, x, target):
     return loss, grad
 
 
-def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update (Kingma & Ba, 2015); t counts from 1."""
-    m = beta1 * m + (1 - beta1) * grad
-    v = beta2 * v + (1 - beta2) * grad * grad
-    mhat = m / (1 - beta1 ** t)
-    vhat = v / (1 - beta2 ** t)
-    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
+KNOTS = H + 1      # knots of the spline start
+HEAD = slice(2 * H + H * H + H, N_PARAMS)   # w3 and b3: the trained parameters
+
+
+def spline_start(x, y):
+    """Parameters of the piecewise-linear interpolant of the points (x, y)
+    (x ascending) at KNOTS knots of evenly spaced index j*(M-1)//H, equal x
+    merged (the later y kept): unit j of layer 1 is relu(x - knot_j), layer 2
+    is the identity, the output weights are the slope changes."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    M = x.shape[0]
+    kx, ky = [], []
+    for j in range(KNOTS if M else 0):
+        i = j * (M - 1) // H if M > 1 else 0
+        if not kx or x[i] > kx[-1]:
+            kx.append(x[i])
+            ky.append(y[i])
+        else:
+            ky[-1] = y[i]
+    segs = max(len(kx) - 1, 0)
+    slope = [(ky[j + 1] - ky[j]) / (kx[j + 1] - kx[j]) for j in range(segs)]
+    W1 = np.array([1.0 if j < segs else 0.0 for j in range(H)])
+    b1 = np.array([-kx[j] if j < segs else -1.0 for j in range(H)])
+    W2 = np.eye(H)
+    b2 = np.zeros(H)
+    w3 = np.array([(slope[0] if j == 0 else slope[j] - slope[j - 1]) if j < segs else 0.0 for j in range(H)])
+    b3 = ky[0] if kx else 0.0
+    return np.concatenate([W1, b1, W2.ravel(), b2, w3, [b3]]), np.array(kx), np.array(ky)
+
+
+def head_step(theta, grad, lr):
+    """One gradient-descent step on the output layer (w3, b3) only."""
+    theta = np.array(theta, dtype=np.float64)
+    theta[HEAD] -= lr * np.asarray(grad, dtype=np.float64)[HEAD]
+    return theta
 
 
 def predict_bucket(theta, x, P):

@@ -87,6 +87,13 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     if (B > pl.Q) return BSPS_ERR_INVALID_ARG;
     pl.B = B;
     pl.P = pl.p * B;
+    // the routing kernel keeps two words per sub-bucket in shared memory:
+    // refine less (larger sub-buckets go to the slower sort tiers) if needed
+    while (prm->refine == 0 && pl.B > 1 && route_smem_bytes(pl) > 227 * 1024) {
+        pl.B /= 2;
+        pl.P = pl.p * pl.B;
+    }
+    B = pl.B;
     if (pl.P > 65535) return BSPS_ERR_TOO_LARGE;  // 16-bit sub-bucket ids
     const double expect = (double)n / pl.P * headroom(B);
     pl.bucket_cl = 8;
@@ -141,7 +148,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take((pl.P + 1) * 8);
     take(pl.P * 4);
     if (pl.classify == BSPS_LEARNED) {
-        take(kParams * 4); take(kParams * 4); take(kParams * 4);
+        take(kParams * 4);
         take((int64_t)kMlpGridMax * (kParams + 1) * 4);
         take(kMlpPointsMax * 4); take(kMlpPointsMax * 4);
         take(8);
@@ -181,15 +188,13 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.slow_list = (uint32_t *)take(pl.P * 4);
     if (pl.classify == BSPS_LEARNED) {
         l.mlp_params = (float *)take(kParams * 4);
-        l.mlp_m = (float *)take(kParams * 4);
-        l.mlp_v = (float *)take(kParams * 4);
         l.mlp_part = (float *)take((int64_t)kMlpGridMax * (kParams + 1) * 4);
         l.mlp_x = (float *)take(kMlpPointsMax * 4);
         l.mlp_y = (float *)take(kMlpPointsMax * 4);
         l.mlp_npts = (int64_t *)take(8);
         l.mlp_norm = (MlpNorm *)take(sizeof(MlpNorm));
     } else {
-        l.mlp_params = l.mlp_m = l.mlp_v = l.mlp_part = l.mlp_x = l.mlp_y = nullptr;
+        l.mlp_params = l.mlp_part = l.mlp_x = l.mlp_y = nullptr;
         l.mlp_npts = nullptr;
         l.mlp_norm = nullptr;
     }

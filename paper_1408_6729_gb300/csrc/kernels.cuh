@@ -86,7 +86,7 @@ struct Layout {
     uint32_t *retry_flag;   // P: the keys-only sort gave the sub-bucket back
     uint32_t *retry_list;   // P
     // learned classifier (classify == BSPS_LEARNED)
-    float *mlp_params, *mlp_m, *mlp_v;   // 1153 each
+    float *mlp_params;                   // 1153
     float *mlp_part;                     // training grid x 1154 partial sums
     float *mlp_x, *mlp_y;                // training points
     int64_t *mlp_npts;
@@ -121,7 +121,7 @@ cudaError_t launch_splitters(const Ctx &c);       // Fig. 1 steps 6-7
 cudaError_t launch_route(const Ctx &c);           // Fig. 1 steps 9-11
 cudaError_t launch_bucket_sort(const Ctx &c);     // Fig. 2 step 12
 cudaError_t launch_debug(const Ctx &c);           // optional diagnostics
-cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, init, Adam
+cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, spline start, training
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);

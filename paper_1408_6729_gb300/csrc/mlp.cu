@@ -1,5 +1,5 @@
 // mlp.cu -- training of the learned bucket classifier on the GPU: loss and
-// gradient (forward and backward written out), Adam, all in one cooperative
+// gradient (forward and backward written out) and gradient steps, all in one cooperative
 // launch; plus the standalone loss/gradient entry point used to check the
 // gradients against the CPU oracle.
 #include <algorithm>
@@ -11,8 +11,13 @@ namespace bsps {
 
 constexpr int kMlpThreads = 128;       // one training point per thread per step
 constexpr int kMlpMaxPoints = kMlpPointsMax;
-constexpr int kMlpSteps = 200;
-constexpr float kMlpLr = 1e-2f;
+constexpr int kMlpSteps = 16;          // gradient steps from the spline start
+// Full-batch gradient descent on the output layer (w3, b3): the loss is a
+// convex quadratic there with Hessian 2 E[h h^T], h = (h2, 1), whose largest
+// eigenvalue is at most 2 * 33 for inputs in [0, 1]; a step below 2/66
+// lowers the loss at every step.
+constexpr float kMlpLr = 0.02f;
+constexpr int kMlpTrainPoints = 4096;  // training points drawn from the sorted sample
 
 // Per-CTA gradient of the mean squared error over the CTA's points
 // [p0, p0+np) (at most kMlpThreads), divided by the global point count m.
@@ -102,7 +107,6 @@ constexpr int kMlpScratchFloats = 4 * kMlpThreads * 33 + 2 * kMlpThreads + 8;
 
 struct MlpTrainArgs {
     float *params;        // kParams, trained in place
-    float *m, *v;         // Adam moments
     float *part;          // grid * (kParams + 1) partial gradients (+ partial loss)
     const float *x, *y;   // training points
     const int64_t *npts;  // number of training points (device)
@@ -112,8 +116,10 @@ struct MlpTrainArgs {
 };
 
 // All training steps in one cooperative launch: every CTA computes the
-// gradient of its points, the grid synchronises, CTA g reduces and applies
-// Adam (Kingma & Ba) to its share of the parameters, the grid synchronises.
+// gradient of its points (all 1153 parameters, the backward pass written
+// out), the grid synchronises, each thread sums the CTAs' partials of one
+// parameter and applies the gradient step to the output layer, the grid
+// synchronises.
 __global__ void __launch_bounds__(kMlpThreads) mlp_train_kernel(MlpTrainArgs a) {
     namespace cg = cooperative_groups;
     auto grid = cg::this_grid();
@@ -149,29 +155,15 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_train_kernel(MlpTrainArgs a) 
             }
             break;
         }
-        // reduce and update this CTA's parameters
-        const float b1c = 1.0f - powf(0.9f, (float)step), b2c = 1.0f - powf(0.999f, (float)step);
-        for (int k = g; k < kParams + 1; k += G) {
-            float s = 0.0f;
-            for (int c = t; c < G; c += kMlpThreads) s += a.part[(int64_t)c * (kParams + 1) + k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if ((t & 31) == 0) red[t >> 5] = s;
-            __syncthreads();
-            if (t == 0) {
-                float gk = 0.0f;
-                for (int i = 0; i < kMlpThreads / 32; ++i) gk += red[i];
-                if (k == kParams) {
-                    if (step == 1 && a.loss_first) *a.loss_first = gk / (float)npts;
-                } else {
-                    const float mk = 0.9f * a.m[k] + 0.1f * gk;
-                    const float vk = 0.999f * a.v[k] + 0.001f * gk * gk;
-                    a.m[k] = mk;
-                    a.v[k] = vk;
-                    a.params[k] -= a.lr * (mk / b1c) / (sqrtf(vk / b2c) + 1e-8f);
-                }
+        // each thread reduces one parameter over the CTAs' partials
+        for (int k = g * kMlpThreads + t; k <= kParams; k += G * kMlpThreads) {
+            float gk = 0.0f;
+            for (int c = 0; c < G; ++c) gk += a.part[(int64_t)c * (kParams + 1) + k];
+            if (k == kParams) {
+                if (step == 1 && a.loss_first) *a.loss_first = gk / (float)npts;
+            } else if (k >= kW3) {
+                a.params[k] -= a.lr * gk;
             }
-            __syncthreads();
         }
         grid.sync();
     }
@@ -206,8 +198,13 @@ __global__ void mlp_grad_reduce_kernel(const float *part, int G, int64_t m, floa
 // ---------------------------------------------------------------------------
 // Training set from the sorted sample and the initial parameters.
 // x_m = normalised value of the sample record of rank r_m (real keys only),
-// y_m = (r_m + 1/2) / S, ranks evenly spaced.  Layer-1 kinks start at the
-// training points' quantiles; the rest is drawn from Philox with the seed.
+// y_m = (r_m + 1/2) / S, ranks evenly spaced.
+//
+// Start: the network is set to the piecewise-linear interpolant of the
+// training points at 33 knots of evenly spaced rank (equal x merged): unit j
+// of layer 1 is relu(x - knot_j), layer 2 passes its input through
+// (W2 = I, b2 = 0; relu is the identity on relu outputs), and the output
+// weights are the slope changes at the knots.  Training then refines it.
 // ---------------------------------------------------------------------------
 template <int DT>
 __global__ void mlp_prepare_kernel(LsdBuffers<typename KeyTraits<DT>::T> b, const int32_t *table, int npos, int64_t S,
@@ -233,11 +230,11 @@ __global__ void mlp_prepare_kernel(LsdBuffers<typename KeyTraits<DT>::T> b, cons
         const double span = vhi - vlo;
         nm.scale = (span > 0 && span < 1e300) ? (float)(1.0 / span) : 0.0f;
         *norm = nm;
-        *npts_out = lo < kMlpMaxPoints ? lo : kMlpMaxPoints;
+        *npts_out = lo < kMlpTrainPoints ? lo : kMlpTrainPoints;
     }
     __syncthreads();
     const int64_t real = s_real;
-    const int64_t M = real < kMlpMaxPoints ? real : kMlpMaxPoints;
+    const int64_t M = real < kMlpTrainPoints ? real : kMlpTrainPoints;
     const MlpNorm nm = *norm;
     for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
         const int64_t r = M > 1 ? i * (real - 1) / (M - 1) : 0;
@@ -249,44 +246,38 @@ __global__ void mlp_prepare_kernel(LsdBuffers<typename KeyTraits<DT>::T> b, cons
     }
 }
 
-__global__ void mlp_init_kernel(const float *x, const int64_t *npts, uint64_t seed, float *params, float *m,
-                                float *v) {
-    const int t = threadIdx.x;  // blockDim >= 64
+__global__ void mlp_init_kernel(const float *x, const float *y, const int64_t *npts, float *params) {
+    const int t = threadIdx.x;  // blockDim >= kH
     const int64_t M = *npts;
-    // uniform draws from Philox4x64-10, key (seed, 1), counter (t, 0, 0, 0)
-    auto unif = [&](int idx) {
-        uint64_t c[4] = {(uint64_t)idx, 0, 0, 0};
-        philox4x64_10(c, seed, 1);
-        return (float)((c[0] >> 40) * (1.0 / 16777216.0));
-    };
-    __shared__ float q[kH], wmax;
-    if (t < kH) q[t] = M > 0 ? x[(int64_t)((t + 0.5) / kH * M)] : (t + 0.5f) / kH;
-    __syncthreads();
+    __shared__ float kx[kH + 1], ky[kH + 1];
+    __shared__ int nk;
     if (t == 0) {
-        float mx = 0.0f;
-        for (int j = 0; j < kH; ++j) {
-            const float gap = fmaxf(q[j] - (j ? q[j - 1] : 0.0f), 1e-6f);
-            mx = fmaxf(mx, 1.0f / gap);
+        int c = 0;
+        for (int j = 0; j <= kH && M > 0; ++j) {
+            const int64_t i = M > 1 ? (int64_t)j * (M - 1) / kH : 0;
+            const float xv = x[i], yv = y[i];
+            if (c == 0 || xv > kx[c - 1]) {
+                kx[c] = xv;
+                ky[c] = yv;
+                ++c;
+            } else {
+                ky[c - 1] = yv;  // equal x: one knot
+            }
         }
-        wmax = mx;
+        nk = c;
     }
     __syncthreads();
+    const int segs = nk > 1 ? nk - 1 : 0;
+    auto slope = [&](int j) { return (ky[j + 1] - ky[j]) / (kx[j + 1] - kx[j]); };
     if (t < kH) {
-        const float gap = fmaxf(q[t] - (t ? q[t - 1] : 0.0f), 1e-6f);
-        const float w1 = (1.0f / gap) / wmax * 50.0f;
-        params[kW1 + t] = w1;
-        params[kB1 + t] = -w1 * q[t];
-        params[kB2 + t] = 0.01f;
-        const float a3 = sqrtf(6.0f / 33.0f);
-        params[kW3 + t] = (2.0f * unif(2048 + t) - 1.0f) * a3;
+        const bool on = t < segs;
+        params[kW1 + t] = on ? 1.0f : 0.0f;
+        params[kB1 + t] = on ? -kx[t] : -1.0f;  // unused units stay at zero
+        params[kB2 + t] = 0.0f;
+        params[kW3 + t] = on ? (t == 0 ? slope(0) : slope(t) - slope(t - 1)) : 0.0f;
     }
-    const float a2 = 0.5f * sqrtf(6.0f / 64.0f);
-    for (int k = t; k < kH * kH; k += blockDim.x) params[kW2 + k] = (2.0f * unif(k) - 1.0f) * a2;
-    if (t == 0) params[kB3] = 0.0f;
-    for (int k = t; k < kParams; k += blockDim.x) {
-        m[k] = 0.0f;
-        v[k] = 0.0f;
-    }
+    for (int k = t; k < kH * kH; k += blockDim.x) params[kW2 + k] = (k / kH == k % kH) ? 1.0f : 0.0f;
+    if (t == 0) params[kB3] = nk > 0 ? ky[0] : 0.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -314,12 +305,9 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     b.tag[1] = c.ly.stag[1];
     mlp_prepare_kernel<DT><<<1, 256, 0, c.stream>>>(b, c.ly.lsd_table, npos, p.sample_size, p.n, c.ly.mlp_norm,
                                                     c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts);
-    mlp_init_kernel<<<1, 256, 0, c.stream>>>(c.ly.mlp_x, c.ly.mlp_npts, p.seed, c.ly.mlp_params, c.ly.mlp_m,
-                                             c.ly.mlp_v);
+    mlp_init_kernel<<<1, 256, 0, c.stream>>>(c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts, c.ly.mlp_params);
     MlpTrainArgs a;
     a.params = c.ly.mlp_params;
-    a.m = c.ly.mlp_m;
-    a.v = c.ly.mlp_v;
     a.part = c.ly.mlp_part;
     a.x = c.ly.mlp_x;
     a.y = c.ly.mlp_y;
@@ -328,7 +316,7 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     a.lr = kMlpLr;
     a.loss_first = c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr;
     a.loss_last = c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr;
-    const int64_t max_pts = std::min<int64_t>(p.sample_size, kMlpMaxPoints);
+    const int64_t max_pts = std::min<int64_t>(p.sample_size, kMlpTrainPoints);
     const int G = std::max(1, std::min(mlp_train_grid(), (int)((max_pts + kMlpThreads - 1) / kMlpThreads)));
     void *args[] = {&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)mlp_train_kernel, dim3(G), dim3(kMlpThreads), args, 0,

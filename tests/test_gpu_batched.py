@@ -174,3 +174,13 @@ def test_autotuned_table_sorts_exactly():
     keys, off = _batch([100, 3000, 9000, 16000, 50000], 51)
     out, sizes, base, _ = _run_batched(keys, off, prm, tune)
     _check(keys, off, out, sizes, base, prm, tune)
+
+
+def test_batched_learned_instances_match_single_calls():
+    bsps = lib()
+    keys, off = _batch([3000, 300000, 140000], 61)
+    prm = bsps.make_params(1, sampling=bsps.BSPS_RANDOM, seed=7)
+    tune = bsps.bsps_tune_default()
+    tune.learned_min_log2 = 18
+    out, sizes, base, _ = _run_batched(keys, off, prm, tune)
+    _check(keys, off, out, sizes, base, prm, tune, oracle_max=0)

@@ -3,8 +3,10 @@
 * gradients against central finite differences of the loss (float64);
 * the network with hand-set weights equals the piecewise-linear function it
   encodes (a closed form);
-* Adam on the empirical CDF of a sorted sample lowers the loss, and the trained
-  network's bucket predictions are closer to the true buckets than a constant;
+* the spline start passes through its knots and is linear between them (the
+  closed form of a piecewise-linear interpolant), and gradient steps on the
+  output layer lower the loss at every step (a convex quadratic with a step
+  below 2/L); the trained predictions beat a constant guess;
 * predictions are clamped to [0, P-1] (NaN -> 0).
 """
 import numpy as np
@@ -50,24 +52,53 @@ def test_hand_set_network_is_its_piecewise_linear_function():
     assert np.allclose(y, np.maximum(x, 0) - np.maximum(x - 0.5, 0))
 
 
-def test_adam_fits_a_cdf():
+def test_spline_start_interpolates_its_knots():
     rng = np.random.default_rng(3)
     keys = np.sort(np.concatenate([rng.normal(0, 1, 3000), rng.normal(8, 0.3, 1000)]))
     x = (keys - keys[0]) / (keys[-1] - keys[0])
     y = (np.arange(x.size) + 0.5) / x.size
-    theta = _theta(4, 0.3)
-    m = np.zeros_like(theta)
-    v = np.zeros_like(theta)
-    l0 = mlp.loss_and_grad(theta, x, y)[0]
-    for t in range(1, 401):
+    theta, kx, ky = mlp.spline_start(x, y)
+    assert len(kx) == mlp.KNOTS
+    f, _ = mlp.forward(theta, kx)
+    assert np.allclose(f, ky, atol=1e-12)
+    mid = (kx[:-1] + kx[1:]) / 2
+    fm, _ = mlp.forward(theta, mid)
+    assert np.allclose(fm, (ky[:-1] + ky[1:]) / 2, atol=1e-12)
+
+
+def test_spline_start_merges_equal_x():
+    x = np.array([0.0, 0.0, 0.0, 0.5, 0.5, 1.0])
+    y = np.array([0.1, 0.2, 0.3, 0.4, 0.5, 0.9])
+    theta, kx, ky = mlp.spline_start(x, y)
+    assert kx.tolist() == [0.0, 0.5, 1.0]
+    f, _ = mlp.forward(theta, kx)
+    assert np.allclose(f, ky)
+
+
+def test_head_steps_lower_the_loss_and_beat_a_constant():
+    rng = np.random.default_rng(5)
+    keys = np.sort(np.concatenate([rng.normal(0, 1, 3000), rng.normal(8, 0.3, 1000)]))
+    x = (keys - keys[0]) / (keys[-1] - keys[0])
+    y = (np.arange(x.size) + 0.5) / x.size
+    theta, _, _ = mlp.spline_start(x, y)
+    losses = []
+    for _ in range(32):
         loss, g = mlp.loss_and_grad(theta, x, y)
-        theta, m, v = mlp.adam_step(theta, g, m, v, t, 1e-2)
-    l1 = mlp.loss_and_grad(theta, x, y)[0]
-    assert l1 < l0 / 20
+        losses.append(loss)
+        theta = mlp.head_step(theta, g, 0.02)
+    assert all(b < a for a, b in zip(losses, losses[1:]))
     P = 64
     true_b = np.minimum((y * P).astype(int), P - 1)
     pred = mlp.predict_bucket(theta, x, P)
     assert np.mean(np.abs(pred - true_b)) < np.mean(np.abs(P // 2 - true_b)) / 4
+
+
+def test_head_step_moves_only_the_output_layer():
+    theta = _theta(6)
+    g = np.ones(mlp.N_PARAMS)
+    t2 = mlp.head_step(theta, g, 0.5)
+    assert np.array_equal(t2[:mlp.HEAD.start], theta[:mlp.HEAD.start])
+    assert np.allclose(t2[mlp.HEAD], theta[mlp.HEAD] - 0.5)
 
 
 def test_prediction_is_clamped():
