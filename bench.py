@@ -41,8 +41,11 @@ WORKLOADS = {
                                             make=lambda n, p, seed: gen.uniform(n, p, seed)),
     "zipf_2e28_int32_pairs_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=True,
                                                make=lambda n, p, seed: gen.zipf(n, seed=seed)),
-    # the 2^26 / p = 1024 shape of the randomized config: same bucket sizes, a
-    # quarter of the data (used for profiling captures)
+    # the 2^28 workload's kernels on a quarter of the data, for full ncu
+    # captures (inputs still larger than L2)
+    "uniform_2e26_int32_p4096_random": dict(n=1 << 26, p=4096, sampling=1, s=0, runs=0, pairs=False,
+                                           make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    # the randomized config's shape: 2^26 keys, p = 1024
     "uniform_2e26_int32_p1024_random": dict(n=1 << 26, p=1024, sampling=1, s=0, runs=0, pairs=False,
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
     # learned classifier against the splitter tree: 2^28 float64 keys of an
@@ -68,7 +71,10 @@ PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
 # ncu capture (profiles/*.md), valid while the kernel source is unchanged.
-NCU_TRAFFIC = {}  # kernel -> (bytes per key, sha256 of the source file at capture)
+# (profiles/*_uniform_2e26_int32_p4096_random.md: 2^26-key captures; both
+# kernels stream every key once, so bytes per key carry over to 2^28)
+NCU_TRAFFIC = {"route_keys_kernel": ((270.733312e6 + 220.545280e6) / (1 << 26), "54aa1426cb9026f3"),
+               "bucket_keys_kernel": ((269.373440e6 + 219.553024e6) / (1 << 26), "a9511cd6edccf126")}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
                                        "paper_1408_6729_gb300/csrc/classify.cuh"],
@@ -86,7 +92,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons every 50 ms (one streaming
+    nvidia-smi process) from the start of the warm-up to the end of the timed
+    region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -94,29 +102,37 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.rows = []
-        self._stop = threading.Event()
+        self.proc = None
         self._t = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self.proc.stdout:
+            line = line.strip()
+            if line:
+                self.rows.append([x.strip() for x in line.split(",")])
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        if self.proc is not None:  # already sampling (started before the warm-up)
+            return self
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)  # the first sample arrives before the work starts
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=10)
+            except Exception:
+                self.proc.kill()
+            self._t.join(timeout=10)
 
     def summary(self):
         if not self.rows:
@@ -126,7 +142,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows), "window": "warm-up and timed region"}
 
 
 def source_hash(paths):
@@ -253,6 +269,7 @@ def run_gpu(args, wl, name):
         if rc:
             raise RuntimeError(bsps.bsps_strerror(rc))
 
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         step()
     st = bsps.bsps_read_stats(ws)
@@ -262,7 +279,7 @@ def run_gpu(args, wl, name):
     # timed region: K whole sorts, back to back on one stream
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total_launches = 0
-    with ClockSampler(local) as clk:
+    with clk:
         barrier(pg)
         torch.cuda.synchronize()
         start.record(stream)
@@ -367,7 +384,8 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     alg_bytes = n * 2 * kb
     achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
     traffic = None
-    if kern in NCU_TRAFFIC and NCU_TRAFFIC[kern][1] == source_hash(KERNEL_SOURCE[kern]):
+    if kern in NCU_TRAFFIC and NCU_TRAFFIC[kern][1] == source_hash(KERNEL_SOURCE[kern]) and \
+            wl.get("dtype") != "f64" and not wl["pairs"]:
         traffic = NCU_TRAFFIC[kern][0] * n
     ms_step = elapsed_ms / args.steps
     value = world * n / (ms_step * 1e-3)
@@ -485,13 +503,14 @@ def run_batched(args, wl, name):
     step()  # records the graph
     torch.cuda.synchronize()
     record_s = time.perf_counter() - t0
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         step()
     st = bsps.bsps_read_stats(ws)
     if st.status:
         raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with clk:
         barrier(pg)
         torch.cuda.synchronize()
         start.record(stream)

@@ -185,6 +185,13 @@ __global__ void __launch_bounds__(256) lsd_scan_kernel(uint32_t *counts, int64_t
     }
 }
 
+// Scatter of one pass: the tile is ranked stably per digit, grouped by digit
+// in shared memory, and each digit's run is written contiguously.
+template <typename K> constexpr size_t lsd_downsweep_smem() {
+    return sizeof(typename BlockRank<kLsdThreads, kLsdItems, 8>::Smem) + 256 * 4 * 2 + 40 * 4 +
+           (size_t)kLsdTile * (sizeof(K) + 4);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kLsdThreads)
 lsd_downsweep_kernel(LsdBuffers<K> b, int64_t S, int pass, const int32_t *table,
@@ -192,9 +199,16 @@ lsd_downsweep_kernel(LsdBuffers<K> b, int64_t S, int pass, const int32_t *table,
     if (pass >= table[0]) return;
     const int q = table[1 + 3 * pass], src = table[2 + 3 * pass], dst = table[3 + 3 * pass];
     using Rank = BlockRank<kLsdThreads, kLsdItems, 8>;
-    __shared__ typename Rank::Smem sm;
-    __shared__ uint32_t base[256];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename Rank::Smem &sm = *reinterpret_cast<typename Rank::Smem *>(smem_raw);
+    uint32_t *base = reinterpret_cast<uint32_t *>(smem_raw + sizeof(typename Rank::Smem));
+    uint32_t *start = base + 256;
+    uint32_t *tmp = start + 256;
+    K *st_f = reinterpret_cast<K *>(tmp + 40);
+    st_f = reinterpret_cast<K *>((reinterpret_cast<uintptr_t>(st_f) + 15) & ~uintptr_t(15));
+    uint32_t *st_t = reinterpret_cast<uint32_t *>(st_f + kLsdTile);
     const int64_t t0 = (int64_t)blockIdx.x * kLsdTile;
+    const int n_here = (int)imin64(kLsdTile, S - t0);
     K f[kLsdItems];
     uint32_t t[kLsdItems], d[kLsdItems], rk[kLsdItems];
 #pragma unroll
@@ -205,20 +219,32 @@ lsd_downsweep_kernel(LsdBuffers<K> b, int64_t S, int pass, const int32_t *table,
             t[i] = b.tag[src][r];
             d[i] = record_digit(f[i], t[i], q);
         } else {
-            d[i] = 255;
+            d[i] = 255;  // after every real record of digit 255 (higher slots)
         }
     }
     Rank::rank(sm, d, rk);
-    for (int dd = threadIdx.x; dd < 256; dd += kLsdThreads) base[dd] = counts[(int64_t)dd * tiles + blockIdx.x];
+    for (int dd = threadIdx.x; dd < 256; dd += kLsdThreads) {
+        base[dd] = counts[(int64_t)dd * tiles + blockIdx.x];
+        start[dd] = sm.digit_tot[dd];
+    }
     __syncthreads();
+    digit_excl_scan<kLsdThreads, 256>(start, tmp);
 #pragma unroll
     for (int i = 0; i < kLsdItems; ++i) {
         const int64_t r = t0 + striped_slot<kLsdThreads, kLsdItems>(i);
         if (r < S) {
-            const uint32_t pos = base[d[i]] + rk[i];
-            b.phi[dst][pos] = f[i];
-            b.tag[dst][pos] = t[i];
+            const uint32_t s = start[d[i]] + rk[i];
+            st_f[s] = f[i];
+            st_t[s] = t[i];
         }
+    }
+    __syncthreads();
+    // staged slot s holds a record of digit dg; its place is base[dg] + s - start[dg]
+    for (int s = threadIdx.x; s < n_here; s += kLsdThreads) {
+        const uint32_t dg = record_digit(st_f[s], st_t[s], q);
+        const uint32_t pos = base[dg] + (uint32_t)s - start[dg];
+        b.phi[dst][pos] = st_f[s];
+        b.tag[dst][pos] = st_t[s];
     }
 }
 
@@ -405,13 +431,16 @@ template <typename K> static cudaError_t launch_sample_sort_t(const Ctx &c, LsdB
                                                                   c.ly.lsd_hist);
     lsd_plan_kernel<K><<<1, 32, 0, c.stream>>>(c.ly.lsd_hist, p.sample_size, c.ly.lsd_table);
     const unsigned tiles = (unsigned)p.lsd_tiles;
+    const size_t dsm = lsd_downsweep_smem<K>() + 16;
+    e = cudaFuncSetAttribute(lsd_downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (e != cudaSuccess) return e;
     for (int pass = 0; pass < NPOS && tiles > 0; ++pass) {
         lsd_upsweep_kernel<K><<<tiles, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
                                                                   c.ly.lsd_counts, p.lsd_tiles);
         lsd_scan_kernel<<<256, 256, 0, c.stream>>>(c.ly.lsd_counts, p.lsd_tiles, pass, c.ly.lsd_table,
                                                    c.ly.lsd_hist);
-        lsd_downsweep_kernel<K><<<tiles, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
-                                                                    c.ly.lsd_counts, p.lsd_tiles);
+        lsd_downsweep_kernel<K><<<tiles, kLsdThreads, dsm, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
+                                                                      c.ly.lsd_counts, p.lsd_tiles);
     }
     return cudaGetLastError();
 }
