@@ -10,10 +10,14 @@
 // holding one distinct key are written out directly, every other bin is given
 // to one CTA, and each CTA copies its stage, bin run by bin run, into the
 // owners' receive buffers.  Each CTA then counting-sorts what it received on
-// up to kCountBits further bits (about one key per count bin) and places the
-// keys that share a count bin by comparison.  A bin too large for one CTA, or
-// count bins longer than kBinMax, make the cluster give the sub-bucket back
-// (returns false) to the stable cluster sort of segsort.cuh.
+// up to kCountBits further bits.  When a count bin spans at most 32 values,
+// two occupancy masks per bin record which values occur at least once and at
+// least twice; in a bin where no value occurs three times a key's place is a
+// sum of popcounts of the masks below its value plus its occurrence index.
+// Keys of other bins are placed by comparison.  A bin too large for one CTA,
+// or count bins longer than kBinMax that need comparisons, make the cluster
+// give the sub-bucket back (returns false) to the stable cluster sort of
+// segsort.cuh.
 #pragma once
 
 #include "radix.cuh"
@@ -26,7 +30,8 @@ struct SegSortKeys {
     static constexpr int V = 16 / (int)sizeof(K);     // keys per 16-byte load
     static constexpr int CAP = T * ITEMS;             // keys one CTA holds
     static constexpr int SB = 8, R = 1 << SB;         // split bins
-    static constexpr int kCountBits = 13, kCountBins = 1 << kCountBits;
+    static constexpr int kCountBits = 12, kCountBins = 1 << kCountBits;
+    static constexpr int kMaskBits = 5;               // count bins of at most 32 values carry masks
     static constexpr uint32_t kBinMax = 64;           // longest count bin ordered by comparison
     static_assert(ITEMS % V == 0, "whole 16-byte loads per thread");
     static_assert(kCountBins % (4 * T) == 0, "whole 16-byte groups of count bins per thread in the scan");
@@ -42,11 +47,14 @@ struct SegSortKeys {
         uint32_t recv[8], own_base[8], ofirst[8], olast[8];
         uint32_t tmp[40];
     };
+    // the count histogram and the two masks (one word per bin) live in the
+    // receive buffer, which is free by then; the buffer is sized for both
+    static constexpr int kM1 = kCountBins + 4, kM2 = kM1 + kCountBins, kScratchWords = kM2 + kCountBins;
+    static constexpr size_t kBufBytes =
+        ((size_t)CAP * sizeof(K) > (size_t)kScratchWords * 4 ? (size_t)CAP * sizeof(K) : (size_t)kScratchWords * 4);
     static constexpr size_t smem_bytes() {
-        return ((sizeof(Smem) + 15) & ~size_t(15)) + 2 * (size_t)CAP * sizeof(K);
+        return ((sizeof(Smem) + 15) & ~size_t(15)) + (size_t)CAP * sizeof(K) + kBufBytes;
     }
-    // the count histogram lives in the receive buffer, which is free by then
-    static_assert((size_t)(kCountBins + 4) * 4 <= (size_t)CAP * sizeof(K), "count bins fit the buffer");
 
     // bin of key k: (k - lo) >> shift, clamped to maxb so that a key outside
     // [lo, hi] can never index past a table
@@ -143,41 +151,68 @@ struct SegSortKeys {
 
     // Sort the keys held in registers (valid where valid(i); all in
     // [lo, lo + 2^bits)) into out[0..n): one counting pass on the top
-    // kCountBits bits, then the place of each key that shares its count bin
-    // by comparison.  chist is free shared memory of kCountBins + 4 words.
+    // kCountBits bits, then each key's place inside its count bin.  scr is free
+    // shared memory of CAP keys.
     template <typename Valid>
     __device__ static bool count_sort(Smem &sm, const K (&k)[ITEMS], Valid valid, K lo, int bits, K *out,
-                                      uint32_t *chist) {
+                                      uint32_t *scr) {
         const int nbb = bits < kCountBits ? bits : kCountBits;
         const int shift = bits - nbb;
         const int nb = 1 << nbb;
-        __syncthreads();  // chist may still be read by the caller
+        const bool masks = shift > 0 && shift <= kMaskBits;
+        uint32_t *chist = scr, *m1 = scr + kM1, *m2 = scr + kM2;
+        __syncthreads();  // scr may still be read by the caller
         for (int b = threadIdx.x; b < nb; b += T) chist[b] = 0;
+        if (masks)
+            for (int b = threadIdx.x; b < nb; b += T) m1[b] = m2[b] = 0;
         __syncthreads();
+        // r: rank inside the count bin (bits 0..27), occurrence of the value (28..29)
         uint32_t r[ITEMS];
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (valid(i)) r[i] = atomicAdd(&chist[bin(k[i], lo, shift, nb - 1)], 1u);
-        __syncthreads();
-        if (!scan_bins(chist, nb, sm.tmp, shift > 0)) return false;
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (valid(i)) {
-                r[i] += chist[bin(k[i], lo, shift, nb - 1)];
-                out[r[i]] = k[i];
-            }
-        if (shift == 0) {  // one value per count bin: placed
-            __syncthreads();
-            return true;
-        }
-        __syncthreads();
-        // place = bin start + keys of the bin below k + equal keys stored before it
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if (valid(i)) {
                 const uint32_t bb = bin(k[i], lo, shift, nb - 1);
+                r[i] = atomicAdd(&chist[bb], 1u);
+                if (masks) {
+                    const uint32_t bit = 1u << (uint32_t)((k[i] - lo) & (K)31);
+                    if (atomicOr(&m1[bb], bit) & bit) r[i] |= (atomicOr(&m2[bb], bit) & bit) ? 2u << 28 : 1u << 28;
+                }
+            }
+        __syncthreads();
+        if (!scan_bins(chist, nb, sm.tmp, shift > kMaskBits)) return false;
+        // keys alone in their bin, or in a bin whose values occur at most
+        // twice, go to their final place; the others wait at bin start + rank
+        bool cmp = false;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i)) {
+                const uint32_t bb = bin(k[i], lo, shift, nb - 1);
+                const uint32_t b0 = chist[bb], len = chist[bb + 1] - b0;
+                uint32_t pos = b0 + (r[i] & 0x0fffffffu);
+                bool fin = shift == 0 || len == 1;
+                if (masks && !fin) {
+                    const uint32_t w1 = m1[bb], w2 = m2[bb];
+                    if ((uint32_t)(__popc(w1) + __popc(w2)) == len) {
+                        const uint32_t below = (1u << (uint32_t)((k[i] - lo) & (K)31)) - 1u;
+                        pos = b0 + __popc(w1 & below) + __popc(w2 & below) + (r[i] >> 28);
+                        fin = true;
+                    }
+                }
+                out[pos] = k[i];
+                r[i] = fin ? 0xffffffffu : pos;
+                cmp |= !fin;
+            }
+        if (!__syncthreads_or(cmp)) return true;
+        // place = bin start + keys of the bin below k + equal keys stored before it
+        bool too_long = false;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (valid(i) && r[i] != 0xffffffffu) {
+                const uint32_t bb = bin(k[i], lo, shift, nb - 1);
                 const uint32_t b0 = chist[bb], b1 = chist[bb + 1], self = r[i];
-                if (b1 - b0 > 1) {
+                if (b1 - b0 > kBinMax) {
+                    too_long = true;
+                } else {
                     uint32_t pos = b0;
                     for (uint32_t y = b0; y < b1; ++y) {
                         const K x = out[y];
@@ -186,10 +221,10 @@ struct SegSortKeys {
                     r[i] = pos;
                 }
             }
-        __syncthreads();
+        if (__syncthreads_or(too_long)) return false;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
-            if (valid(i)) out[r[i]] = k[i];
+            if (valid(i) && r[i] != 0xffffffffu) out[r[i]] = k[i];
         __syncthreads();
         return true;
     }
