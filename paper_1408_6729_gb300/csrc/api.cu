@@ -214,6 +214,7 @@ static int kernels_per_call(const Plan &pl) {
     int k = 1;                                   // sample (random draw or block sort)
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
+    if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
     k += pl.pairs ? 2 : 3;                       // cluster bucket sort tiers, out-of-core bucket sort

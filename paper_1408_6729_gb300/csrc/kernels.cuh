@@ -125,6 +125,7 @@ cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: trainin
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);
+bool msd_sample_sort(const Plan &p);               // MSD sample sort is launched (32-bit keys, large samples)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
 size_t route_keys_smem_bytes(const Plan &pl);
 

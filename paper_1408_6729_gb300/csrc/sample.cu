@@ -101,18 +101,37 @@ __global__ void lsd_hist_kernel(const K *__restrict__ phi, const uint32_t *__res
         const uint32_t v = (&h[0][0])[i];
         if (v) atomicAdd(&hist[i], v);
     }
+    if constexpr (sizeof(K) == 4) {  // value range of the sample, for the MSD sort
+        uint32_t mn_inv = 0, mx = 0;
+        for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S;
+             r += (int64_t)gridDim.x * blockDim.x) {
+            const uint32_t f = (uint32_t)phi[r];
+            mn_inv = max(mn_inv, ~f);
+            mx = max(mx, f);
+        }
+        mn_inv = __reduce_max_sync(0xffffffffu, mn_inv);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&hist[NPOS * 256], mn_inv);
+            atomicMax(&hist[NPOS * 256 + 1], mx);
+        }
+    }
 }
 
 // table[0] = passes; then (position, src, dst) per pass; table[1+3*NPOS] = final buffer
 template <typename K>
 __global__ void lsd_plan_kernel(const uint32_t *hist, int64_t S, int32_t *table) {
     constexpr int NPOS = 4 + (int)sizeof(K);
+    __shared__ int trivial[NPOS];
+    if (threadIdx.x < NPOS) trivial[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NPOS * 256; i += blockDim.x)
+        if ((int64_t)hist[i] == S) trivial[i / 256] = 1;  // every record has this byte
+    __syncthreads();
     if (threadIdx.x != 0) return;
     int np = 0, cur = 0;
     for (int q = 0; q < NPOS; ++q) {
-        bool trivial = false;
-        for (int d = 0; d < 256; ++d) trivial |= (int64_t)hist[q * 256 + d] == S;
-        if (trivial) continue;
+        if (trivial[q]) continue;
         table[1 + 3 * np] = q;
         table[2 + 3 * np] = cur;
         table[3 + 3 * np] = 1 - cur;
@@ -130,15 +149,18 @@ lsd_upsweep_kernel(const LsdBuffers<K> b, int64_t S, int pass, const int32_t *ta
     if (pass >= table[0]) return;
     const int q = table[1 + 3 * pass], src = table[2 + 3 * pass];
     __shared__ uint32_t h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * kLsdTile;
-    for (int i = threadIdx.x; i < kLsdTile; i += kLsdThreads) {
-        const int64_t r = t0 + i;
-        if (r < S) atomicAdd(&h[record_digit(b.phi[src][r], b.tag[src][r], q)], 1u);
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        const int64_t t0 = tile * kLsdTile;
+        for (int i = threadIdx.x; i < kLsdTile; i += kLsdThreads) {
+            const int64_t r = t0 + i;
+            if (r < S) atomicAdd(&h[record_digit(b.phi[src][r], b.tag[src][r], q)], 1u);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) counts[(int64_t)d * tiles + tile] = h[d];
+        __syncthreads();
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) counts[(int64_t)d * tiles + blockIdx.x] = h[d];
 }
 
 // Exclusive scan of the per-tile counts of one digit (CTA d scans digit d)
@@ -207,44 +229,350 @@ lsd_downsweep_kernel(LsdBuffers<K> b, int64_t S, int pass, const int32_t *table,
     K *st_f = reinterpret_cast<K *>(tmp + 40);
     st_f = reinterpret_cast<K *>((reinterpret_cast<uintptr_t>(st_f) + 15) & ~uintptr_t(15));
     uint32_t *st_t = reinterpret_cast<uint32_t *>(st_f + kLsdTile);
-    const int64_t t0 = (int64_t)blockIdx.x * kLsdTile;
-    const int n_here = (int)imin64(kLsdTile, S - t0);
-    K f[kLsdItems];
-    uint32_t t[kLsdItems], d[kLsdItems], rk[kLsdItems];
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t t0 = tile * kLsdTile;
+        const int n_here = (int)imin64(kLsdTile, S - t0);
+        K f[kLsdItems];
+        uint32_t t[kLsdItems], d[kLsdItems], rk[kLsdItems];
 #pragma unroll
-    for (int i = 0; i < kLsdItems; ++i) {
-        const int64_t r = t0 + striped_slot<kLsdThreads, kLsdItems>(i);
-        if (r < S) {
-            f[i] = b.phi[src][r];
-            t[i] = b.tag[src][r];
-            d[i] = record_digit(f[i], t[i], q);
-        } else {
-            d[i] = 255;  // after every real record of digit 255 (higher slots)
+        for (int i = 0; i < kLsdItems; ++i) {
+            const int64_t r = t0 + striped_slot<kLsdThreads, kLsdItems>(i);
+            if (r < S) {
+                f[i] = b.phi[src][r];
+                t[i] = b.tag[src][r];
+                d[i] = record_digit(f[i], t[i], q);
+            } else {
+                d[i] = 255;  // after every real record of digit 255 (higher slots)
+            }
         }
+        Rank::rank(sm, d, rk);
+        for (int dd = threadIdx.x; dd < 256; dd += kLsdThreads) {
+            base[dd] = counts[(int64_t)dd * tiles + tile];
+            start[dd] = sm.digit_tot[dd];
+        }
+        __syncthreads();
+        digit_excl_scan<kLsdThreads, 256>(start, tmp);
+#pragma unroll
+        for (int i = 0; i < kLsdItems; ++i) {
+            const int64_t r = t0 + striped_slot<kLsdThreads, kLsdItems>(i);
+            if (r < S) {
+                const uint32_t s = start[d[i]] + rk[i];
+                st_f[s] = f[i];
+                st_t[s] = t[i];
+            }
+        }
+        __syncthreads();
+        // staged slot s holds a record of digit dg; its place is base[dg] + s - start[dg]
+        for (int s = threadIdx.x; s < n_here; s += kLsdThreads) {
+            const uint32_t dg = record_digit(st_f[s], st_t[s], q);
+            const uint32_t pos = base[dg] + (uint32_t)s - start[dg];
+            b.phi[dst][pos] = st_f[s];
+            b.tag[dst][pos] = st_t[s];
+        }
+        __syncthreads();
     }
-    Rank::rank(sm, d, rk);
-    for (int dd = threadIdx.x; dd < 256; dd += kLsdThreads) {
-        base[dd] = counts[(int64_t)dd * tiles + blockIdx.x];
-        start[dd] = sm.digit_tot[dd];
+}
+
+// ---------------------------------------------------------------------------
+// MSD sample sort for 32-bit keys: records are put into 2^BITS bins (4096 up
+// to 8M records, 8192 above) by the top BITS bits of phi - min(phi) in one staged pass, and every bin is sorted in
+// shared memory by (phi, tag).  Used when no bin holds more than kMsdBinMax
+// records; otherwise the LSD passes above run.  Both give the same (unique)
+// sorted sample.
+//
+// Table slots: [kMsdFlag] = 1 when this path is taken, [kMsdShift] = bin
+// shift, [kMsdMin] = min(phi).  Scratch in the LSD tile counts: bin counts
+// [0, B), bin starts [B, 2B+1), bin cursors [2B+4, 3B+4), B = 2^BITS.
+// ---------------------------------------------------------------------------
+constexpr int kMsdBinMax = 4096;  // records one CTA sorts in shared memory
+constexpr int kMsdFlag = 40, kMsdShift = 41, kMsdMin = 42;
+constexpr int64_t kMsdWideSample = 8 << 20;  // samples above this use 8192 bins
+template <int BITS> struct Msd {
+    static constexpr int kBins = 1 << BITS, kStart = kBins, kCursor = 2 * kBins + 4;
+};
+constexpr int64_t kMsdMinSample = 1 << 19;  // smaller samples: the LSD passes
+
+__device__ __forceinline__ uint32_t msd_bin(uint32_t f, uint32_t mn, int shift) {
+    return (f - mn) >> shift;  // < Msd<BITS>::kBins by the choice of shift
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(256) msd_hist_kernel(const uint32_t *__restrict__ phi, int64_t S,
+                                                       const uint32_t *lsd_hist, int npos, uint32_t *counts) {
+    __shared__ uint32_t h[Msd<BITS>::kBins];
+    for (int i = threadIdx.x; i < Msd<BITS>::kBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t mn = ~lsd_hist[npos * 256], mx = lsd_hist[npos * 256 + 1];
+    const int bl = bit_length<uint32_t>(mx - mn);
+    const int shift = bl > BITS ? bl - BITS : 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < S; r += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[msd_bin(phi[r], mn, shift)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < Msd<BITS>::kBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], h[i]);
+}
+
+// Bin starts; the MSD path is taken when every bin fits one CTA.
+template <int BITS>
+__global__ void __launch_bounds__(1024) msd_plan_kernel(uint32_t *counts, const uint32_t *lsd_hist, int npos,
+                                                        int32_t *table) {
+    __shared__ uint32_t tmp[40];
+    __shared__ int big;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) big = 0;
+    __syncthreads();
+    constexpr int PER = Msd<BITS>::kBins / 1024;
+    uint32_t v[PER], local = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        v[q] = counts[tid * PER + q];
+        local += v[q];
+        if (v[q] > (uint32_t)kMsdBinMax) big = 1;
+    }
+    uint32_t wt;
+    const uint32_t we = warp_excl_scan(local, &wt);
+    if (lane == 31) tmp[warp] = wt;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t;
+        const uint32_t e = warp_excl_scan(tmp[lane], &t);
+        tmp[lane] = e;
     }
     __syncthreads();
-    digit_excl_scan<kLsdThreads, 256>(start, tmp);
+    uint32_t run = tmp[warp] + we;
 #pragma unroll
-    for (int i = 0; i < kLsdItems; ++i) {
-        const int64_t r = t0 + striped_slot<kLsdThreads, kLsdItems>(i);
-        if (r < S) {
-            const uint32_t s = start[d[i]] + rk[i];
-            st_f[s] = f[i];
-            st_t[s] = t[i];
+    for (int q = 0; q < PER; ++q) {
+        counts[Msd<BITS>::kStart + tid * PER + q] = run;
+        counts[Msd<BITS>::kCursor + tid * PER + q] = 0;
+        run += v[q];
+    }
+    if (tid == 1023) counts[Msd<BITS>::kStart + Msd<BITS>::kBins] = run;
+    if (tid == 0) {
+        const uint32_t mn = ~lsd_hist[npos * 256], mx = lsd_hist[npos * 256 + 1];
+        const int bl = bit_length<uint32_t>(mx - mn);
+        const bool take = !big;
+        table[kMsdFlag] = take ? 1 : 0;
+        table[kMsdShift] = bl > BITS ? bl - BITS : 0;
+        table[kMsdMin] = (int32_t)mn;
+        if (take) {
+            table[0] = 0;              // no LSD passes
+            table[1 + 3 * npos] = 1;   // the sorted sample ends in buffer 1
+        }
+    }
+}
+
+// Records of a tile, grouped by bin in shared memory, each bin's run written
+// contiguously at its bin start plus a reserved offset.
+constexpr int kMsdThreads = 512, kMsdItems = 16, kMsdTile = kMsdThreads * kMsdItems;
+template <int BITS>
+__global__ void __launch_bounds__(kMsdThreads) msd_scatter_kernel(LsdBuffers<uint32_t> b, int64_t S,
+                                                                  const int32_t *table, uint32_t *counts) {
+    if (table[kMsdFlag] == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);      // Msd<BITS>::kBins + 4
+    uint32_t *dlt = cnt + Msd<BITS>::kBins + 4;                           // Msd<BITS>::kBins
+    uint32_t *st_f = dlt + Msd<BITS>::kBins;                              // kMsdTile
+    uint32_t *st_t = st_f + kMsdTile;                             // kMsdTile
+    uint16_t *st_b = reinterpret_cast<uint16_t *>(st_t + kMsdTile);  // kMsdTile
+    __shared__ uint32_t tmp[40];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = table[kMsdShift];
+    const uint32_t mn = (uint32_t)table[kMsdMin];
+    const int64_t t0 = (int64_t)blockIdx.x * kMsdTile;
+    const int nh = (int)imin64(kMsdTile, S - t0);
+    for (int i = tid; i < Msd<BITS>::kBins; i += kMsdThreads) cnt[i] = 0;
+    __syncthreads();
+    uint32_t f[kMsdItems], t[kMsdItems], br[kMsdItems];
+#pragma unroll
+    for (int i = 0; i < kMsdItems; ++i) {
+        const int s = i * kMsdThreads + tid;
+        if (s < nh) {
+            f[i] = b.phi[0][t0 + s];
+            t[i] = b.tag[0][t0 + s];
+            const uint32_t bin = msd_bin(f[i], mn, shift);
+            br[i] = bin << 16 | atomicAdd(&cnt[bin], 1u);
         }
     }
     __syncthreads();
-    // staged slot s holds a record of digit dg; its place is base[dg] + s - start[dg]
-    for (int s = threadIdx.x; s < n_here; s += kLsdThreads) {
-        const uint32_t dg = record_digit(st_f[s], st_t[s], q);
-        const uint32_t pos = base[dg] + (uint32_t)s - start[dg];
-        b.phi[dst][pos] = st_f[s];
-        b.tag[dst][pos] = st_t[s];
+    // starts of the bins inside the tile (8 bins per thread) and reservations
+    constexpr int PER = Msd<BITS>::kBins / kMsdThreads;
+    uint32_t c[PER], local = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        c[q] = cnt[tid * PER + q];
+        local += c[q];
+    }
+    uint32_t wt;
+    const uint32_t we = warp_excl_scan(local, &wt);
+    if (lane == 31) tmp[warp] = wt;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t tt;
+        const uint32_t e = warp_excl_scan(lane < kMsdThreads / 32 ? tmp[lane] : 0u, &tt);
+        if (lane < kMsdThreads / 32) tmp[lane] = e;
+    }
+    __syncthreads();
+    uint32_t run = tmp[warp] + we;
+    uint32_t at[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) at[q] = c[q] ? atomicAdd(&counts[Msd<BITS>::kCursor + tid * PER + q], c[q]) : 0u;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int bin = tid * PER + q;
+        cnt[bin] = run;
+        dlt[bin] = counts[Msd<BITS>::kStart + bin] + at[q] - run;  // output slot of tile position s: dlt + s
+        run += c[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kMsdItems; ++i) {
+        const int s = i * kMsdThreads + tid;
+        if (s < nh) {
+            const uint32_t bin = br[i] >> 16, pos = cnt[bin] + (br[i] & 0xffffu);
+            st_f[pos] = f[i];
+            st_t[pos] = t[i];
+            st_b[pos] = (uint16_t)bin;
+        }
+    }
+    __syncthreads();
+    for (int s = tid; s < nh; s += kMsdThreads) {
+        const uint32_t o = dlt[st_b[s]] + (uint32_t)s;
+        b.phi[1][o] = st_f[s];
+        b.tag[1][o] = st_t[s];
+    }
+}
+template <int BITS>
+constexpr size_t msd_scatter_smem() { return (size_t)(2 * Msd<BITS>::kBins + 4 + 2 * kMsdTile) * 4 + (size_t)kMsdTile * 2; }
+
+// One bin per CTA, (phi, tag) as one 64-bit key: a counting pass on the top
+// 11 bits of the bin's range, then each key's place inside its count bin by
+// comparison; a bin whose count bins are too long is sorted by a bitonic
+// network instead.  (Sampling with replacement can repeat a record: equal
+// keys are ordered by their slot.)
+constexpr int kMsdLocalThreads = 512, kMsdLocalItems = kMsdBinMax / kMsdLocalThreads;
+constexpr int kMsdCountBits = 11, kMsdCountBins = 1 << kMsdCountBits;
+template <int BITS>
+__global__ void __launch_bounds__(kMsdLocalThreads) msd_local_kernel(LsdBuffers<uint32_t> b, const int32_t *table,
+                                                                      const uint32_t *counts) {
+    if (table[kMsdFlag] == 0) return;
+    __shared__ uint64_t a[kMsdBinMax];
+    __shared__ uint32_t ch[kMsdCountBins + 4];
+    __shared__ uint32_t tmp[40];
+    constexpr int T = kMsdLocalThreads, IT = kMsdLocalItems;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lo = counts[Msd<BITS>::kStart + blockIdx.x], hi = counts[Msd<BITS>::kStart + blockIdx.x + 1];
+    const int n = (int)(hi - lo);
+    if (n <= 1) return;
+    // keys of this bin lie in [klo, khi]
+    const int shift = table[kMsdShift];
+    const uint32_t mn = (uint32_t)table[kMsdMin];
+    const uint64_t flo = (uint64_t)mn + ((uint64_t)blockIdx.x << shift);
+    const uint64_t klo = flo << 32, span = (((uint64_t)1 << shift) << 32) - 1;
+    const int bits = bit_length<uint64_t>(span);
+    const int sh = bits > kMsdCountBits ? bits - kMsdCountBits : 0;
+    uint64_t k[IT];
+    uint32_t r[IT];
+    for (int i = tid; i < kMsdCountBins; i += T) ch[i] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = i * T + tid;
+        if (e < n) {
+            k[i] = (uint64_t)b.phi[1][lo + e] << 32 | b.tag[1][lo + e];
+            const uint64_t d = (k[i] - klo) >> sh;
+            r[i] = atomicAdd(&ch[d < kMsdCountBins ? (uint32_t)d : kMsdCountBins - 1], 1u);
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the count bins (8 per thread), longest bin
+    constexpr int PER = kMsdCountBins / T;
+    uint32_t v[PER], loc = 0, mx = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        v[q] = ch[tid * PER + q];
+        loc += v[q];
+        mx = max(mx, v[q]);
+    }
+    uint32_t wt;
+    const uint32_t we = warp_excl_scan(loc, &wt);
+    if (lane == 31) tmp[warp] = wt;
+    const bool too_long = __syncthreads_or(mx > 64);
+    if (!too_long) {
+        if (warp == 0) {
+            uint32_t t;
+            const uint32_t e = warp_excl_scan(lane < T / 32 ? tmp[lane] : 0u, &t);
+            if (lane < T / 32) tmp[lane] = e;
+        }
+        __syncthreads();
+        uint32_t run = tmp[warp] + we;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            ch[tid * PER + q] = run;
+            run += v[q];
+        }
+        if (tid == 0) ch[kMsdCountBins] = (uint32_t)n;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = i * T + tid;
+            if (e < n) {
+                const uint64_t d = (k[i] - klo) >> sh;
+                r[i] += ch[d < kMsdCountBins ? (uint32_t)d : kMsdCountBins - 1];
+                a[r[i]] = k[i];
+            }
+        }
+        __syncthreads();
+        // keys sharing a count bin: place = bin start + smaller keys in the bin
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = i * T + tid;
+            if (e < n) {
+                const uint64_t d = (k[i] - klo) >> sh;
+                const uint32_t cb = d < kMsdCountBins ? (uint32_t)d : kMsdCountBins - 1;
+                const uint32_t b0 = ch[cb], b1 = ch[cb + 1], self = r[i];
+                if (b1 - b0 > 1) {
+                    uint32_t pos = b0;
+                    for (uint32_t y = b0; y < b1; ++y) {
+                        const uint64_t x = a[y];
+                        pos += (x < k[i]) | ((x == k[i]) & (y < self));
+                    }
+                    r[i] = pos;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+            if (i * T + tid < n) a[r[i]] = k[i];
+        __syncthreads();
+    } else {
+        int n2 = 1;
+        while (n2 < n) n2 <<= 1;
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = i * T + tid;
+            if (e < n) a[e] = k[i];
+        }
+        for (int e = n + tid; e < n2; e += T) a[e] = ~0ull;
+        __syncthreads();
+        for (int kk = 2; kk <= n2; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int t = tid; t < (n2 >> 1); t += T) {
+                    const int i = 2 * t - (t & (j - 1));
+                    const int l = i + j;
+                    const bool up = (i & kk) == 0;
+                    const uint64_t x = a[i], y = a[l];
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    for (int i = tid; i < n; i += T) {
+        b.phi[1][lo + i] = (uint32_t)(a[i] >> 32);
+        b.tag[1][lo + i] = (uint32_t)a[i];
     }
 }
 
@@ -421,28 +749,65 @@ cudaError_t launch_sample(const Ctx &c) {
     }
 }
 
+template <int BITS> static cudaError_t launch_msd(const Ctx &c, LsdBuffers<uint32_t> b, int hist_blocks) {
+    const Plan &p = c.pl;
+    constexpr int NPOS = 8;
+    uint32_t *cnt = c.ly.lsd_counts;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, Msd<BITS>::kBins * sizeof(uint32_t), c.stream);
+    if (e != cudaSuccess) return e;
+    msd_hist_kernel<BITS><<<max(hist_blocks, 1), 256, 0, c.stream>>>(b.phi[0], p.sample_size, c.ly.lsd_hist, NPOS,
+                                                                    cnt);
+    msd_plan_kernel<BITS><<<1, 1024, 0, c.stream>>>(cnt, c.ly.lsd_hist, NPOS, c.ly.lsd_table);
+    e = cudaFuncSetAttribute(msd_scatter_kernel<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)msd_scatter_smem<BITS>());
+    if (e != cudaSuccess) return e;
+    const unsigned mt = (unsigned)((p.sample_size + kMsdTile - 1) / kMsdTile);
+    msd_scatter_kernel<BITS><<<mt, kMsdThreads, msd_scatter_smem<BITS>(), c.stream>>>(b, p.sample_size,
+                                                                                        c.ly.lsd_table, cnt);
+    msd_local_kernel<BITS><<<Msd<BITS>::kBins, kMsdLocalThreads, 0, c.stream>>>(b, c.ly.lsd_table, cnt);
+    return cudaGetLastError();
+}
+
 template <typename K> static cudaError_t launch_sample_sort_t(const Ctx &c, LsdBuffers<K> b) {
     const Plan &p = c.pl;
     constexpr int NPOS = 4 + (int)sizeof(K);
-    cudaError_t e = cudaMemsetAsync(c.ly.lsd_hist, 0, NPOS * 256 * sizeof(uint32_t), c.stream);
+    cudaError_t e = cudaMemsetAsync(c.ly.lsd_hist, 0, (NPOS * 256 + 2) * sizeof(uint32_t), c.stream);
     if (e != cudaSuccess) return e;
     const int hist_blocks = (int)imin64(1024, (p.sample_size + 1023) / 1024);
     lsd_hist_kernel<K><<<max(hist_blocks, 1), 256, 0, c.stream>>>(b.phi[0], b.tag[0], p.sample_size,
                                                                   c.ly.lsd_hist);
-    lsd_plan_kernel<K><<<1, 32, 0, c.stream>>>(c.ly.lsd_hist, p.sample_size, c.ly.lsd_table);
+    lsd_plan_kernel<K><<<1, 256, 0, c.stream>>>(c.ly.lsd_hist, p.sample_size, c.ly.lsd_table);
+    if constexpr (sizeof(K) == 4) {
+        if (msd_sample_sort(p)) {
+            e = p.sample_size > kMsdWideSample ? launch_msd<13>(c, b, hist_blocks) : launch_msd<12>(c, b, hist_blocks);
+            if (e != cudaSuccess) return e;
+        }
+    }
     const unsigned tiles = (unsigned)p.lsd_tiles;
     const size_t dsm = lsd_downsweep_smem<K>() + 16;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned lsd_grid = (unsigned)std::min<int64_t>(p.lsd_tiles, 2 * (int64_t)std::max(sms, 1));
     e = cudaFuncSetAttribute(lsd_downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (e != cudaSuccess) return e;
     for (int pass = 0; pass < NPOS && tiles > 0; ++pass) {
-        lsd_upsweep_kernel<K><<<tiles, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
-                                                                  c.ly.lsd_counts, p.lsd_tiles);
+        lsd_upsweep_kernel<K><<<lsd_grid, kLsdThreads, 0, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
+                                                                     c.ly.lsd_counts, p.lsd_tiles);
         lsd_scan_kernel<<<256, 256, 0, c.stream>>>(c.ly.lsd_counts, p.lsd_tiles, pass, c.ly.lsd_table,
                                                    c.ly.lsd_hist);
-        lsd_downsweep_kernel<K><<<tiles, kLsdThreads, dsm, c.stream>>>(b, p.sample_size, pass, c.ly.lsd_table,
-                                                                      c.ly.lsd_counts, p.lsd_tiles);
+        lsd_downsweep_kernel<K><<<lsd_grid, kLsdThreads, dsm, c.stream>>>(b, p.sample_size, pass,
+                                                                         c.ly.lsd_table, c.ly.lsd_counts,
+                                                                         p.lsd_tiles);
     }
     return cudaGetLastError();
+}
+
+bool msd_sample_sort(const Plan &p) {
+    // large samples of 32-bit keys; the tile counts double as the MSD scratch
+    const int64_t need = p.sample_size > kMsdWideSample ? Msd<13>::kCursor + Msd<13>::kBins
+                                                        : Msd<12>::kCursor + Msd<12>::kBins;
+    return p.key_bytes == 4 && p.sample_size >= kMsdMinSample && std::max<int64_t>(p.lsd_tiles, 1) * 256 >= need;
 }
 
 cudaError_t launch_sample_sort(const Ctx &c) {
