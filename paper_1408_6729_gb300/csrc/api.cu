@@ -142,6 +142,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(pairs ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     take(pl.P * 4);
     take(pl.P * 4); take(pl.P * 4);
+    take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
     take(pl.P * pl.cap * pl.key_bytes + 64);
     take(pairs ? pl.P * pl.cap * 4 : 0);
     take(pl.P * 4);
@@ -181,6 +182,7 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.cursor = (uint32_t *)take(pl.P * 4);
     l.retry_flag = (uint32_t *)take(pl.P * 4);
     l.retry_list = (uint32_t *)take(pl.P * 4);
+    l.run_retry = (uint32_t *)take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
     l.reg_keys = take(pl.P * pl.cap * pl.key_bytes + 64);
     l.reg_vals = (uint32_t *)take(pl.pairs ? pl.P * pl.cap * 4 : 0);
     l.vsize = (uint32_t *)take(pl.P * 4);
@@ -212,6 +214,7 @@ static void to_public(const Plan &p, bsps_plan *out) {
 // slots whose byte position is constant return at once).
 static int kernels_per_call(const Plan &pl) {
     int k = 1;                                   // sample (random draw or block sort)
+    if (run_keys_cluster(pl)) k += 1;            // keys-only block sort before the stable one
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts

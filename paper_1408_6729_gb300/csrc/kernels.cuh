@@ -85,6 +85,7 @@ struct Layout {
     uint32_t *cursor;       // P keys routed per sub-bucket
     uint32_t *retry_flag;   // P: the keys-only sort gave the sub-bucket back
     uint32_t *retry_list;   // P
+    uint32_t *run_retry;    // R: blocks the keys-only block sort gave back
     // learned classifier (classify == BSPS_LEARNED)
     float *mlp_params;                   // 1153
     float *mlp_part;                     // training grid x 1154 partial sums
@@ -125,7 +126,8 @@ cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: trainin
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);
-bool msd_sample_sort(const Plan &p);               // MSD sample sort is launched (32-bit keys, large samples)
+bool msd_sample_sort(const Plan &p);
+int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)               // MSD sample sort is launched (32-bit keys, large samples)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
 size_t route_keys_smem_bytes(const Plan &pl);
 

@@ -2,6 +2,7 @@
 // 3-7, Fig. 3 steps 3-9) and the optional diagnostics.
 #include "classify.cuh"
 #include "segsort.cuh"
+#include "segsort_keys.cuh"
 
 namespace bsps {
 
@@ -39,9 +40,10 @@ template <int DT, int CL, int ITEMS>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSortThreads, 1)
 run_sample_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m,
                   int64_t M, int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag,
-                  uint32_t *too_big) {
+                  uint32_t *too_big, const uint32_t *only) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSort<K, true, CL, ITEMS>;
+    if (only && only[blockIdx.x / CL] == 0) return;  // only the blocks the keys-only sort gave back
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
     K *buf = reinterpret_cast<K *>(smem_raw + ((sizeof(typename SS::Smem) + 15) & ~size_t(15)));
@@ -70,6 +72,75 @@ run_sample_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n,
     };
     if (!SS::run(sm, buf, slots, len, load, emit) && threadIdx.x == 0 && blockIdx.x % CL == 0)
         atomicExch(too_big, 1u);
+}
+
+// The same sample from a faster sort: for 32-bit keys, (phi << 32 | position
+// in the block) is unique, so the keys-only cluster sort of segsort_keys.cuh
+// orders the block exactly as the stable sort does.  A block it gives back
+// is flagged and sorted by run_sample_kernel.
+constexpr int kRunKeysItems = 20;  // 512 threads x 20 = 10240 keys per CTA (room for uneven owners)
+template <int DT, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 1)
+run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t M,
+                       int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry) {
+    using K = typename KeyTraits<DT>::T;
+    static_assert(sizeof(K) == 4, "32-bit keys and 32-bit positions in one word");
+    using SS = SegSortKeys<uint64_t, CL, kRunKeysItems>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t k = blockIdx.x / CL;
+    const int64_t lo = k * m;
+    const int64_t len = lo < n ? imin64(m, n - lo) : 0;
+    if (blockIdx.x % CL == 0) {  // pads: sorted positions len..M-1, in tag order
+        for (int64_t j = 1 + threadIdx.x; j <= s; j += blockDim.x) {
+            const int64_t pos = j * x - 1;
+            if (pos >= len) {
+                sphi[k * s + (j - 1)] = all_ones<K>();
+                stag[k * s + (j - 1)] = (uint32_t)(n + k * M + pos);
+            }
+        }
+    }
+    if (len == 0) return;
+    {
+        // 64 evenly spaced keys of the block: many repeats mean many equal
+        // keys, whose order by position the counting finish cannot resolve;
+        // such a block goes to the stable sort at once (every CTA of the
+        // cluster reads the same keys and decides alike)
+        __shared__ uint32_t probe[64];
+        __shared__ int repeats;
+        if (threadIdx.x < 64) probe[threadIdx.x] = (uint32_t)KeyTraits<DT>::phi(keys[lo + threadIdx.x * len / 64]);
+        if (threadIdx.x == 0) repeats = 0;
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            bool seen = false;
+            for (int j = 0; j < (int)threadIdx.x; ++j) seen |= probe[j] == probe[threadIdx.x];
+            if (seen) atomicAdd(&repeats, 1);
+        }
+        __syncthreads();
+        if (len >= 64 && repeats > 8) {
+            if (threadIdx.x == 0) retry[k] = 1u;
+            return;
+        }
+    }
+    auto loadf = [&](uint64_t (&kk)[kRunKeysItems], int64_t e0, int cnt) {
+#pragma unroll
+        for (int i = 0; i < kRunKeysItems; ++i) {
+            const int e = SS::lidx(i);
+            if (e < cnt) kk[i] = (uint64_t)KeyTraits<DT>::phi(keys[lo + e0 + e]) << 32 | (uint32_t)(e0 + e);
+        }
+    };
+    auto emit = [&](uint32_t pos, uint64_t key) {
+        if ((pos + 1) % x == 0) {
+            const int64_t j = (pos + 1) / x;
+            sphi[k * s + (j - 1)] = (K)(key >> 32);
+            stag[k * s + (j - 1)] = (uint32_t)(lo + (uint32_t)key);
+        }
+    };
+    // a split bin of one key value (many equal keys) is ordered by position
+    // only, which the counting finish cannot resolve: leave such blocks to the
+    // stable sort at once
+    auto one_value = [](uint64_t mn, uint64_t mx) { return (mn >> 32) == (mx >> 32); };
+    if (!SS::run_load(smem_raw, len, 0ull, ~0ull, loadf, emit, one_value) && threadIdx.x == 0)
+        atomicExch(&retry[k], 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,7 +777,7 @@ template <int DT> static LsdBuffers<typename KeyTraits<DT>::T> lsd_buffers(const
     return b;
 }
 
-template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const Ctx &c) {
+template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const Ctx &c, const uint32_t *only) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSort<K, true, CL, ITEMS>;
     const size_t smem = SS::smem_bytes();
@@ -716,8 +787,31 @@ template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const 
     const Plan &p = c.pl;
     kern<<<(unsigned)(p.R * CL), kSortThreads, smem, c.stream>>>(
         (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0],
-        (uint32_t *)&c.ly.status->run_too_big);
+        (uint32_t *)&c.ly.status->run_too_big, only);
     return cudaGetLastError();
+}
+
+template <int DT, int CL> static cudaError_t launch_run_sample_keys(const Ctx &c) {
+    using K = typename KeyTraits<DT>::T;
+    using SS = SegSortKeys<uint64_t, CL, kRunKeysItems>;
+    const size_t smem = SS::smem_bytes();
+    auto kern = run_sample_keys_kernel<DT, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const Plan &p = c.pl;
+    e = cudaMemsetAsync(c.ly.run_retry, 0, (size_t)p.R * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(p.R * CL), 512, smem, c.stream>>>((const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x,
+                                                        (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
+    return cudaGetLastError();
+}
+
+// cluster size of the keys-only block sort (0: not used)
+int run_keys_cluster(const Plan &p) {
+    if (p.sampling != BSPS_REGULAR || p.key_bytes != 4 || p.m >= ((int64_t)1 << 32)) return 0;
+    for (int cl = 1; cl <= 8; cl *= 2)
+        if (p.m <= (int64_t)cl * 512 * kRunKeysItems) return cl;
+    return 0;
 }
 
 template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
@@ -730,12 +824,24 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
             (const K *)c.keys_in, p.n, p.sample_size, p.seed, (K *)c.ly.sphi[0], c.ly.stag[0]);
         return cudaGetLastError();
     }
+    const uint32_t *only = nullptr;
+    if constexpr (sizeof(K) == 4) {
+        cudaError_t e = cudaSuccess;
+        switch (run_keys_cluster(p)) {
+        case 0: break;
+        case 1: e = launch_run_sample_keys<DT, 1>(c); only = c.ly.run_retry; break;
+        case 2: e = launch_run_sample_keys<DT, 2>(c); only = c.ly.run_retry; break;
+        case 4: e = launch_run_sample_keys<DT, 4>(c); only = c.ly.run_retry; break;
+        default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
+        }
+        if (e != cudaSuccess) return e;
+    }
     constexpr int IT = sizeof(K) == 8 ? kRunItems64 : kRunItems32;
     switch (p.run_cl) {
-    case 1: return launch_run_sample<DT, 1, IT>(c);
-    case 2: return launch_run_sample<DT, 2, IT>(c);
-    case 4: return launch_run_sample<DT, 4, IT>(c);
-    case 8: return launch_run_sample<DT, 8, IT>(c);
+    case 1: return launch_run_sample<DT, 1, IT>(c, only);
+    case 2: return launch_run_sample<DT, 2, IT>(c, only);
+    case 4: return launch_run_sample<DT, 4, IT>(c, only);
+    case 8: return launch_run_sample<DT, 8, IT>(c, only);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -46,6 +46,7 @@ struct SegSortKeys {
         int32_t owner[R];    // -1: bin with one distinct key (or none)
         uint32_t recv[8], own_base[8], ofirst[8], olast[8];
         uint32_t tmp[40];
+        uint32_t heavy;      // keys in bins the caller's give_up predicate marks
     };
     // the count histogram and the two masks (one word per bin) live in the
     // receive buffer, which is free by then; the buffer is sized for both
@@ -237,6 +238,19 @@ struct SegSortKeys {
     // receive buffer (CAP keys each).
     template <typename Emit>
     __device__ static bool run(unsigned char *smem, const K *__restrict__ gsrc, int64_t cnt, K lo, K hi, Emit emit) {
+        auto from_global = [&](K (&k)[ITEMS], int64_t e0, int n) { load(k, gsrc + e0, n); };
+        auto never = [](K, K) { return false; };
+        return run_load(smem, cnt, lo, hi, from_global, emit, never);
+    }
+
+    // As run(), with the keys of positions [e0, e0 + n) produced by
+    // load(k, e0, n) into register i of each thread for position e0 + lidx(i).
+    // give_up(min, max) marks split bins the caller expects to be slow here;
+    // when they hold more than a quarter of the keys the sub-bucket is given
+    // back right after the split.
+    template <typename Load, typename Emit, typename GiveUp>
+    __device__ static bool run_load(unsigned char *smem, int64_t cnt, K lo, K hi, Load loadf, Emit emit,
+                                    GiveUp give_up) {
         Smem &sm = *reinterpret_cast<Smem *>(smem);
         K *stage = reinterpret_cast<K *>(smem + ((sizeof(Smem) + 15) & ~size_t(15)));
         K *buf = stage + CAP;
@@ -248,7 +262,7 @@ struct SegSortKeys {
         const int mycnt = (int)imax64(0, imin64(share, cnt - e0));
         const int bits = bit_length<K>(hi - lo);
         K k[ITEMS];
-        load(k, gsrc + e0, mycnt);
+        loadf(k, e0, mycnt);
         auto mine = [&](int i) { return lidx(i) < mycnt; };
         if (bits == 0) {  // one distinct key
 #pragma unroll
@@ -276,6 +290,7 @@ struct SegSortKeys {
                 sm.ofirst[tid] = 0xffffffffu;
                 sm.olast[tid] = 0;
             }
+            if (tid == 0) sm.heavy = 0;
             __syncthreads();
             uint32_t r[ITEMS];
 #pragma unroll
@@ -310,6 +325,7 @@ struct SegSortKeys {
                 }
             }
             const bool flat = tot == 0 || gmin == gmax;
+            if (!flat && give_up(gmin, gmax)) atomicAdd(&sm.heavy, tot);
             if (tid < R) {
                 sm.pre[tid] = pre;
                 sm.start[tid] = tot;
@@ -335,7 +351,7 @@ struct SegSortKeys {
             }
             __syncthreads();
             if (tid < R && sm.owner[tid] >= 0) sm.dst[tid] -= sm.own_base[sm.owner[tid]];
-            bool bail = false;
+            bool bail = (int64_t)sm.heavy * 4 > cnt;
 #pragma unroll
             for (int q = 0; q < CL; ++q) bail |= sm.recv[q] > (uint32_t)CAP;
             if (bail) {  // uniform: every CTA saw the same counts
