@@ -221,7 +221,7 @@ static int kernels_per_call(const Plan &pl) {
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
     k += pl.pairs ? 2 : 3;                       // cluster bucket sort tiers, out-of-core bucket sort
-    if (pl.classify == BSPS_LEARNED) k += 3;     // training set, initial weights, training
+    if (pl.classify == BSPS_LEARNED) k += 4;     // training set, spline start, features, output-layer steps
     return k;
 }
 

@@ -88,7 +88,7 @@ struct Layout {
     uint32_t *run_retry;    // R: blocks the keys-only block sort gave back
     // learned classifier (classify == BSPS_LEARNED)
     float *mlp_params;                   // 1153
-    float *mlp_part;                     // training grid x 1154 partial sums
+    float *mlp_part;                     // layer-2 features of the training points (points x 32)
     float *mlp_x, *mlp_y;                // training points
     int64_t *mlp_npts;
     struct MlpNorm *mlp_norm;

@@ -1,9 +1,9 @@
-// mlp.cu -- training of the learned bucket classifier on the GPU: loss and
-// gradient (forward and backward written out) and gradient steps, all in one cooperative
-// launch; plus the standalone loss/gradient entry point used to check the
-// gradients against the CPU oracle.
+// mlp.cu -- training of the learned bucket classifier on the GPU: the training
+// set from the sorted sample, the spline start, the layer-2 features of every
+// training point, and full-batch gradient steps on the output layer; plus the
+// loss and gradient of the whole network (forward and backward written out)
+// behind the entry point that checks them against the CPU oracle.
 #include <algorithm>
-#include <cooperative_groups.h>
 
 #include "mlp.cuh"
 
@@ -105,68 +105,85 @@ __device__ float mlp_cta_grad(const float *w, const float *__restrict__ x, const
 
 constexpr int kMlpScratchFloats = 4 * kMlpThreads * 33 + 2 * kMlpThreads + 8;
 
-struct MlpTrainArgs {
-    float *params;        // kParams, trained in place
-    float *part;          // grid * (kParams + 1) partial gradients (+ partial loss)
-    const float *x, *y;   // training points
-    const int64_t *npts;  // number of training points (device)
-    int steps;
-    float lr;
-    float *loss_first, *loss_last;  // nullable
-};
-
-// All training steps in one cooperative launch: every CTA computes the
-// gradient of its points (all 1153 parameters, the backward pass written
-// out), the grid synchronises, each thread sums the CTAs' partials of one
-// parameter and applies the gradient step to the output layer, the grid
-// synchronises.
-__global__ void __launch_bounds__(kMlpThreads) mlp_train_kernel(MlpTrainArgs a) {
-    namespace cg = cooperative_groups;
-    auto grid = cg::this_grid();
+// Layers 1 and 2 stay at their start; their output for every training point
+// is computed once.  h2 holds kH x npts floats (feature-major, so that the
+// training steps read consecutive points).
+__global__ void __launch_bounds__(kMlpThreads) mlp_features_kernel(const float *params, const float *x,
+                                                                  const int64_t *npts, float *h2) {
     __shared__ float w[kParams + 3];
-    __shared__ float scratch[kMlpScratchFloats];
-    __shared__ float red[kMlpThreads / 32];
-    const int G = gridDim.x, g = blockIdx.x, t = threadIdx.x;
-    const int64_t npts = *a.npts;
-    if (npts == 0) return;  // nothing to learn from (uniform across the grid)
-    const int64_t per = (npts + G - 1) / G;
-    const int64_t p0 = g * per;
-    const int np = (int)imax64(0, imin64(per, npts - p0));
-    for (int step = 1; step <= a.steps + 1; ++step) {
-        for (int k = t; k < kParams; k += kMlpThreads) w[k] = a.params[k];
-        __syncthreads();
-        float *part = a.part + (int64_t)g * (kParams + 1);
-        const float lp = mlp_cta_grad(w, a.x, a.y, p0, np, npts, part, scratch);
-        if (t == 0) part[kParams] = lp;
-        grid.sync();
-        if (step == a.steps + 1) {   // final pass only measures the loss
-            if (g == 0) {
-                float l = 0.0f;
-                for (int c = t; c < G; c += kMlpThreads) l += a.part[(int64_t)c * (kParams + 1) + kParams];
+    for (int k = threadIdx.x; k < kParams; k += kMlpThreads) w[k] = params[k];
+    __syncthreads();
+    const int64_t m = *npts;
+    for (int64_t p = (int64_t)blockIdx.x * kMlpThreads + threadIdx.x; p < m; p += (int64_t)gridDim.x * kMlpThreads) {
+        const float xi = x[p];
+        float h1[kH];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-                if ((t & 31) == 0) red[t >> 5] = l;
-                __syncthreads();
-                if (t == 0 && a.loss_last) {
-                    float s = 0.0f;
-                    for (int i = 0; i < kMlpThreads / 32; ++i) s += red[i];
-                    *a.loss_last = s / (float)npts;
-                }
-            }
-            break;
+        for (int j = 0; j < kH; ++j) h1[j] = fmaxf(fmaf(w[kW1 + j], xi, w[kB1 + j]), 0.0f);
+        for (int i = 0; i < kH; ++i) {
+            float z = w[kB2 + i];
+#pragma unroll
+            for (int j = 0; j < kH; ++j) z = fmaf(w[kW2 + i * kH + j], h1[j], z);
+            h2[(int64_t)i * m + p] = fmaxf(z, 0.0f);
         }
-        // each thread reduces one parameter over the CTAs' partials
-        for (int k = g * kMlpThreads + t; k <= kParams; k += G * kMlpThreads) {
-            float gk = 0.0f;
-            for (int c = 0; c < G; ++c) gk += a.part[(int64_t)c * (kParams + 1) + k];
-            if (k == kParams) {
-                if (step == 1 && a.loss_first) *a.loss_first = gk / (float)npts;
-            } else if (k >= kW3) {
-                a.params[k] -= a.lr * gk;
-            }
-        }
-        grid.sync();
     }
+}
+
+// Full-batch gradient descent on the output layer (w3, b3) from the cached
+// features, one CTA: every step sums 2 r h2 / m and 2 r / m over the points
+// (r = y - target) and moves w3, b3 against them.  Records the loss before the
+// first step and after the last.
+constexpr int kMlpHeadThreads = 1024;
+__global__ void __launch_bounds__(kMlpHeadThreads) mlp_head_kernel(float *params, const float *h2, const float *y,
+                                                                   const int64_t *npts, int steps, float lr,
+                                                                   float *loss_first, float *loss_last) {
+    constexpr int W = kMlpHeadThreads / 32, NV = kH + 2;  // w3 gradient, b3 gradient, loss
+    __shared__ float head[kH + 1];
+    __shared__ float part[W][NV];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t m = *npts;
+    if (m == 0) return;
+    if (t <= kH) head[t] = params[kW3 + t];  // w3[0..31], b3
+    __syncthreads();
+    for (int step = 0; step <= steps; ++step) {
+        float g[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) g[i] = 0.0f;
+        for (int64_t p = t; p < m; p += kMlpHeadThreads) {
+            float f[kH];
+#pragma unroll
+            for (int i = 0; i < kH; ++i) f[i] = h2[(int64_t)i * m + p];
+            float out = head[kH];
+#pragma unroll
+            for (int i = 0; i < kH; ++i) out = fmaf(head[i], f[i], out);
+            const float r = out - y[p];
+            const float dy = 2.0f * r / (float)m;
+#pragma unroll
+            for (int i = 0; i < kH; ++i) g[i] = fmaf(dy, f[i], g[i]);
+            g[kH] += dy;
+            g[kH + 1] = fmaf(r, r, g[kH + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) g[i] += __shfl_xor_sync(0xffffffffu, g[i], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) part[warp][i] = g[i];
+        __syncthreads();
+        if (t < NV) {
+            float tot = 0.0f;
+            for (int q = 0; q < W; ++q) tot += part[q][t];
+            if (t == kH + 1) {
+                if (step == 0 && loss_first) *loss_first = tot / (float)m;
+                if (step == steps && loss_last) *loss_last = tot / (float)m;
+            } else if (step < steps) {
+                head[t] -= lr * tot;  // t < kH: w3[t]; t == kH: b3
+            }
+        }
+        __syncthreads();
+    }
+    if (t <= kH) params[kW3 + t] = head[t];
 }
 
 // Loss and gradient only (for the gradient check against the CPU oracle).
@@ -283,17 +300,6 @@ __global__ void mlp_init_kernel(const float *x, const float *y, const int64_t *n
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-int mlp_train_grid() {
-    static int cached = 0;
-    if (cached) return cached;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp_train_kernel, kMlpThreads, 0);
-    cached = std::max(1, std::min(std::min(sms * std::max(occ, 1), kMlpMaxPoints / kMlpThreads), kMlpGridMax));
-    return cached;
-}
-
 template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     using K = typename KeyTraits<DT>::T;
     const Plan &p = c.pl;
@@ -306,22 +312,13 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     mlp_prepare_kernel<DT><<<1, 256, 0, c.stream>>>(b, c.ly.lsd_table, npos, p.sample_size, p.n, c.ly.mlp_norm,
                                                     c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts);
     mlp_init_kernel<<<1, 256, 0, c.stream>>>(c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts, c.ly.mlp_params);
-    MlpTrainArgs a;
-    a.params = c.ly.mlp_params;
-    a.part = c.ly.mlp_part;
-    a.x = c.ly.mlp_x;
-    a.y = c.ly.mlp_y;
-    a.npts = c.ly.mlp_npts;
-    a.steps = kMlpSteps;
-    a.lr = kMlpLr;
-    a.loss_first = c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr;
-    a.loss_last = c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr;
     const int64_t max_pts = std::min<int64_t>(p.sample_size, kMlpTrainPoints);
-    const int G = std::max(1, std::min(mlp_train_grid(), (int)((max_pts + kMlpThreads - 1) / kMlpThreads)));
-    void *args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mlp_train_kernel, dim3(G), dim3(kMlpThreads), args, 0,
-                                                c.stream);
-    if (e != cudaSuccess) return e;
+    const int fgrid = (int)std::max<int64_t>(1, (max_pts + kMlpThreads - 1) / kMlpThreads);
+    mlp_features_kernel<<<fgrid, kMlpThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_x, c.ly.mlp_npts, c.ly.mlp_part);
+    mlp_head_kernel<<<1, kMlpHeadThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_part, c.ly.mlp_y, c.ly.mlp_npts,
+                                                         kMlpSteps, kMlpLr, c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr,
+                                                         c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr);
+    cudaError_t e = cudaGetLastError();
     if (c.dbg.mlp_params)
         e = cudaMemcpyAsync(c.dbg.mlp_params, c.ly.mlp_params, sizeof(float) * kParams, cudaMemcpyDeviceToDevice,
                             c.stream);
