@@ -73,8 +73,8 @@ PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "
 # ncu capture (profiles/*.md), valid while the kernel source is unchanged.
 # (profiles/*_uniform_2e26_int32_p4096_random.md: 2^26-key captures; both
 # kernels stream every key once, so bytes per key carry over to 2^28)
-NCU_TRAFFIC = {"route_keys_kernel": ((270.733312e6 + 220.545280e6) / (1 << 26), "54aa1426cb9026f3"),
-               "bucket_keys_kernel": ((269.373440e6 + 219.553024e6) / (1 << 26), "a9511cd6edccf126")}
+NCU_TRAFFIC = {"route_keys_kernel": ((270.544128e6 + 220.683520e6) / (1 << 26), "54aa1426cb9026f3"),
+               "bucket_keys_kernel": ((269.037568e6 + 218.690304e6) / (1 << 26), "e5632899d558dff5")}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
                                        "paper_1408_6729_gb300/csrc/classify.cuh"],
