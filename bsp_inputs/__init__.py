@@ -82,6 +82,53 @@ def staggered(n: int, p: int, seed: int = 1) -> np.ndarray:
     return _per_block(n, p, seed, fill)
 
 
+def g_group(n: int, p: int, seed: int = 1, g: int = 2) -> np.ndarray:
+    """[g-G]: blocks are taken g at a time; block i of group j = i // g splits
+    its keys into g runs, run t uniform on slice k = (j*g + p/2 + t) mod p of
+    p equal slices of [0, INT_MAX) (slice k = [k*INT_MAX/p, (k+1)*INT_MAX/p - 1])."""
+    def fill(gen_, i, c):
+        j = i // g
+        out = np.empty(c, np.int64)
+        per = -(-c // g)
+        for t in range(g):
+            a, b = t * per, min(c, (t + 1) * per)
+            if b > a:
+                k = (j * g + p // 2 + t) % p
+                lo, hi = k * INT_MAX // p, (k + 1) * INT_MAX // p
+                out[a:b] = gen_.integers(lo, max(hi, lo + 1), size=b - a, dtype=np.int64)
+        return out
+    return _per_block(n, p, seed, fill)
+
+
+def det_duplicates(n: int, p: int, seed: int = 1) -> np.ndarray:
+    """[DD]: the first p/2 blocks hold only the value lg n, the next p/4
+    blocks only lg(n/p), the next p/8 only lg(n/p^2), and so on while a
+    whole block group is left; in the last block the first n/(2p) keys are
+    lg(n/p), the next n/(4p) lg(n/(2p)), and so on, the final keys taking
+    the last value.  lg x is floor(log2 x) (negative below 1).  No randomness."""
+    def lg(x: float) -> int:
+        return int(np.floor(np.log2(x)))
+    out = np.empty(n, np.int32)
+    blocks = list(_blocks(n, p))
+    b, i = 0, 1
+    while b < p - 1:
+        cnt = max(1, p >> i)
+        cnt = min(cnt, p - 1 - b)
+        for q in range(b, b + cnt):
+            _, lo, hi = blocks[q]
+            out[lo:hi] = lg(n / float(p) ** (i - 1))
+        b += cnt
+        i += 1
+    _, lo, hi = blocks[p - 1]
+    pos, i = lo, 1
+    while pos < hi:
+        c = max(1, (hi - lo) >> i)
+        out[pos:min(hi, pos + c)] = lg(n / (p * 2.0 ** (i - 1)))
+        pos += c
+        i += 1
+    return out
+
+
 def zero_entropy(n: int, value: int = 2**30) -> np.ndarray:
     """Every key equal."""
     return np.full(n, value, np.int32)
@@ -119,6 +166,12 @@ def batched_sizes(count: int, lo_log2: float = 8.0, hi_log2: float = 22.0, seed:
     u = _rng(seed, 17).uniform(lo_log2, hi_log2, count)
     return np.floor(2.0 ** u).astype(np.int64)
 
+
+# the paper's other inputs (Sec. 6.3), beside the five of the 2^26 config
+EXTRA_DISTRIBUTIONS = {
+    "two_group": lambda n, p, seed: g_group(n, p, seed, 2),
+    "det_duplicates": lambda n, p, seed: det_duplicates(n, p, seed),
+}
 
 DISTRIBUTIONS = {
     "uniform": lambda n, p, seed: uniform(n, p, seed),

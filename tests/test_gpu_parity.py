@@ -88,11 +88,14 @@ def test_single_bucket(mode):
     assert_same(gpu, ref)
 
 
+ALL_DISTRIBUTIONS = {**gen.DISTRIBUTIONS, **gen.EXTRA_DISTRIBUTIONS}
+
+
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
-@pytest.mark.parametrize("name", sorted(gen.DISTRIBUTIONS))
+@pytest.mark.parametrize("name", sorted(ALL_DISTRIBUTIONS))
 def test_distributions_2e20(mode, name):
     n, p = 1 << 20, 256
-    keys = gen.DISTRIBUTIONS[name](n, p, 1)
+    keys = ALL_DISTRIBUTIONS[name](n, p, 1)
     vals = np.arange(n, dtype=np.uint32)
     ref = ref_sort(keys, p, 0, 0, mode, 21, vals)
     gpu = run_gpu(keys, p, 0, 0, mode, 21, vals)
