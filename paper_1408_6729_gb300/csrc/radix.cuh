@@ -1,10 +1,10 @@
-// radix.cuh -- stable on-chip radix ranking and the cluster radix sort.
+// radix.cuh -- stable on-chip radix ranking.
 //
-// Used for every "Sort_Seq" of the paper (Fig. 1 step 3 and Fig. 2 step 12):
-// the sort of a block of keys for regular sampling, the sort of every bucket
-// after routing, and the tile step of the sample sort.  The paper's local sort
-// is stable (Sec. 5.1.1); so is this one: an LSD radix sort whose per-digit
-// ranking keeps input order among equal digits.
+// The building block of the stable sorts (the paper's local sort is stable,
+// Sec. 5.1.1): the stable cluster sort of segsort.cuh (blocks for regular
+// sampling, buckets with payloads), the stable partition of the routing with
+// payloads, and the scatter of the LSD sample sort.  Ranks keep input order
+// among equal digits.
 #pragma once
 
 #include "common.cuh"
@@ -143,130 +143,5 @@ __device__ __forceinline__ void digit_excl_scan(uint32_t *v, uint32_t *tmp) {
     if (tid < RADIX) v[tid] = e + tmp[warp];
     __syncthreads();
 }
-
-// ---------------------------------------------------------------------------
-// Cluster radix sort: CL CTAs of one thread-block cluster sort up to
-// CL*THREADS*ITEMS keys (with an optional 32-bit companion, e.g. the input
-// slot) held in their shared memory.  CTA c holds positions [c*CAP, (c+1)*CAP)
-// before and after the sort.  Each pass ranks locally, exchanges the per-digit
-// totals through distributed shared memory, and scatters every key into the
-// shared memory of the CTA that owns its new position.
-// ---------------------------------------------------------------------------
-template <typename K, bool HAS_V, int THREADS, int ITEMS, int CL>
-struct ClusterSort {
-    static constexpr int CAP = THREADS * ITEMS;
-    static constexpr int RADIX_BITS = 8, RADIX = 256;
-    using Rank = BlockRank<THREADS, ITEMS, RADIX_BITS>;
-    struct Smem {
-        typename Rank::Smem rank;
-        uint32_t base[RADIX];
-        uint32_t prefix[RADIX];   // keys of this digit held by lower-ranked CTAs
-        uint32_t tmp[40];
-        K red_min, red_max;
-    };
-
-    // Sort keys[0..CAP) (and vals) of every CTA of the cluster by their low
-    // `bits` bits.  Unused slots must hold all-ones keys and sit after the
-    // used ones in slot order.
-    __device__ static void sort(Smem &sm, K *keys, uint32_t *vals, int bits) {
-        auto cluster = cg::this_cluster();
-        const unsigned my_rank = CL > 1 ? cluster.block_rank() : 0;
-        for (int shift = 0; shift < bits; shift += RADIX_BITS) {
-            K k[ITEMS];
-            uint32_t v[ITEMS], d[ITEMS], rk[ITEMS];
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const int s = striped_slot<THREADS, ITEMS>(i);
-                k[i] = keys[s];
-                if constexpr (HAS_V) v[i] = vals[s];
-                d[i] = (uint32_t)(k[i] >> shift) & (RADIX - 1);
-            }
-            Rank::rank(sm.rank, d, rk);
-            if constexpr (CL > 1) {
-                cluster.sync();  // every CTA's totals are final and its items are in registers
-                for (int dd = threadIdx.x; dd < RADIX; dd += THREADS) {
-                    uint32_t before = 0, total = 0;
-#pragma unroll
-                    for (int r = 0; r < CL; ++r) {
-                        const uint32_t t = *cluster.map_shared_rank(&sm.rank.digit_tot[dd], r);
-                        before += (unsigned)r < my_rank ? t : 0;
-                        total += t;
-                    }
-                    sm.base[dd] = total;
-                    sm.prefix[dd] = before;
-                }
-                __syncthreads();
-            } else {
-                for (int dd = threadIdx.x; dd < RADIX; dd += THREADS) sm.base[dd] = sm.rank.digit_tot[dd];
-                __syncthreads();
-            }
-            digit_excl_scan<THREADS, RADIX>(sm.base, sm.tmp);
-            if constexpr (CL > 1) {
-                for (int dd = threadIdx.x; dd < RADIX; dd += THREADS) sm.base[dd] += sm.prefix[dd];
-                __syncthreads();
-            }
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t pos = sm.base[d[i]] + rk[i];
-                if constexpr (CL > 1) {
-                    const unsigned owner = pos / CAP, slot = pos % CAP;
-                    K *dk = cluster.map_shared_rank(keys, owner);
-                    dk[slot] = k[i];
-                    if constexpr (HAS_V) {
-                        uint32_t *dv = cluster.map_shared_rank(vals, owner);
-                        dv[slot] = v[i];
-                    }
-                } else {
-                    keys[pos] = k[i];
-                    if constexpr (HAS_V) vals[pos] = v[i];
-                }
-            }
-            if constexpr (CL > 1) cluster.sync();
-            else __syncthreads();
-        }
-    }
-
-    // Cluster-wide min and max of per-thread values (all threads call).
-    __device__ static void minmax(Smem &sm, K lo, K hi, K &out_lo, K &out_hi) {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            K a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
-            lo = a < lo ? a : lo;
-            hi = b > hi ? b : hi;
-        }
-        if (threadIdx.x == 0) { sm.red_min = all_ones<K>(); sm.red_max = 0; }
-        __syncthreads();
-        if (lane == 0) {
-            if constexpr (sizeof(K) == 8) {
-                atomicMin((unsigned long long *)&sm.red_min, (unsigned long long)lo);
-                atomicMax((unsigned long long *)&sm.red_max, (unsigned long long)hi);
-            } else {
-                atomicMin((unsigned *)&sm.red_min, (unsigned)lo);
-                atomicMax((unsigned *)&sm.red_max, (unsigned)hi);
-            }
-        }
-        if constexpr (CL > 1) {
-            auto cluster = cg::this_cluster();
-            cluster.sync();
-            K a = all_ones<K>(), b = 0;
-#pragma unroll
-            for (int r = 0; r < CL; ++r) {
-                const K x = *cluster.map_shared_rank(&sm.red_min, r);
-                const K y = *cluster.map_shared_rank(&sm.red_max, r);
-                a = x < a ? x : a;
-                b = y > b ? y : b;
-            }
-            out_lo = a;
-            out_hi = b;
-            cluster.sync();  // nobody rewrites red_min/red_max while others read
-        } else {
-            __syncthreads();
-            out_lo = sm.red_min;
-            out_hi = sm.red_max;
-            __syncthreads();
-        }
-    }
-};
 
 } // namespace bsps
