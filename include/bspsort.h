@@ -195,10 +195,12 @@ int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream);
 
 /*
  * Learned classifier (params.classify = BSPS_LEARNED; not in the paper).  A
- * 1->32->32->1 ReLU network (FP32) is trained on the sample the method draws
- * (the empirical CDF of the sorted sample), predicts each key's sub-bucket as
- * floor(P * y), and a bounded search against the true splitters corrects every
- * prediction, so all results equal those of BSPS_TREE.  Parameters are packed
+ * 1->32->32->1 ReLU network (FP32) fits the empirical CDF of the sorted sample
+ * the method draws: it starts as the piecewise-linear interpolant of up to
+ * 4096 sample points at 33 knots and its output layer is then trained by
+ * full-batch gradient descent on the GPU.  It predicts each key's sub-bucket
+ * as floor(P * y), and a bounded search against the true splitters corrects
+ * every prediction, so all results equal those of BSPS_TREE.  Parameters are packed
  * as W1[32] b1[32] W2[32][32] (row i = unit i of layer 2) b2[32] w3[32] b3.
  *
  * bsps_mlp_loss_grad -- mean squared error of the network `d_params` on the m
