@@ -201,3 +201,54 @@ def test_zipf_pairs_regular_p4096_2e24():
     ref = oracle.sort(keys, p, p, p, oracle.REGULAR, 0, vals=vals, want_sample=True)
     gpu = run_gpu(keys, p, p, p, oracle.REGULAR, 0, vals, bucket_of=False)
     assert_same(gpu, ref)
+
+
+def test_msd_sample_sort_4096_bins():
+    """Random sample of 991,231 records (>= 2^19): the MSD sample sort with 4096
+    bins; every sample record and splitter against the oracle."""
+    n, p = 1 << 22, 1024
+    keys = gen.uniform(n, p, 4)
+    ref = oracle.sort(keys, p, 0, 0, oracle.RANDOM, 9, want_sample=True)
+    gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 9, bucket_of=False)
+    assert gpu.plan.sample_size == 2 * 22 * 22 * p - 1
+    assert_same(gpu, ref)
+
+
+def test_msd_sample_sort_8192_bins_regular():
+    """Regular sample of 16.8M records (> 8M): 8192 MSD bins, and the keys-only
+    block sort of (phi, position) words for the 4096 blocks."""
+    n, p = 1 << 24, 4096
+    keys = gen.uniform(n, p, 5)
+    ref = oracle.sort(keys, p, p, p, oracle.REGULAR, 0, want_sample=True)
+    gpu = run_gpu(keys, p, p, p, oracle.REGULAR, 0, bucket_of=False)
+    assert gpu.plan.sample_size == p * p
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("m", [81920, 81919, 40961])
+def test_block_sort_at_cluster_capacity(m):
+    """Blocks of exactly the keys-only block sort's cluster capacity (8 x 10240),
+    one key less (a pad per block), and one key past a 4-CTA cluster."""
+    R = p = 4
+    keys = gen.uniform(R * m, R, 6)
+    ref = ref_sort(keys, p, 32, R, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, p, 32, R, oracle.REGULAR, 0)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("runs", [8, 2])
+def test_block_sort_float_total_order_and_duplicates(runs):
+    """float32 blocks with -0/+0, infinities and repeated values through the
+    keys-only block sort of (phi, position) words (regular sampling; one CTA
+    per block, and clusters of 4)."""
+    rng = np.random.default_rng(8)
+    n, p = 1 << 16, 8
+    keys = rng.normal(0, 1, n).astype(np.float32)
+    keys[::97] = -0.0
+    keys[1::97] = 0.0
+    keys[2::101] = np.inf
+    keys[3::101] = -np.inf
+    keys[4::7] = keys[5::7][: len(keys[4::7])]
+    ref = ref_sort(keys, p, 64, runs, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, p, 64, runs, oracle.REGULAR, 0)
+    assert_same(gpu, ref)
