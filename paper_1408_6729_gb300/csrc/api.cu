@@ -214,7 +214,7 @@ static void to_public(const Plan &p, bsps_plan *out) {
 // slots whose byte position is constant return at once).
 static int kernels_per_call(const Plan &pl) {
     int k = 1;                                   // sample (random draw or block sort)
-    if (run_keys_cluster(pl)) k += 1;            // keys-only block sort before the stable one
+    if (run_keys_cluster(pl)) k += 2;            // keys-only and few-values block samplers before the stable one
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts

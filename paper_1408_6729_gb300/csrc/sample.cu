@@ -128,9 +128,10 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
             if (e < cnt) kk[i] = (uint64_t)KeyTraits<DT>::phi(keys[lo + e0 + e]) << 32 | (uint32_t)(e0 + e);
         }
     };
+    const uint32_t xx = (uint32_t)x;
     auto emit = [&](uint32_t pos, uint64_t key) {
-        if ((pos + 1) % x == 0) {
-            const int64_t j = (pos + 1) / x;
+        if ((pos + 1) % xx == 0) {
+            const int64_t j = (pos + 1) / xx;
             sphi[k * s + (j - 1)] = (K)(key >> 32);
             stag[k * s + (j - 1)] = (uint32_t)(lo + (uint32_t)key);
         }
@@ -148,6 +149,147 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 // bytes of tag, then of phi.  Byte positions on which every record agrees are
 // skipped; the pass table is built on the device.
 // ---------------------------------------------------------------------------
+// Blocks of few distinct keys (regular sampling, 32-bit keys): a block's
+// sorted order by (phi, tag) is its distinct values in order, each repeated in
+// position order.  One CTA counts the values in a shared-memory hash table,
+// ranks the distinct values, and then walks the block in position order: the
+// sorted rank of a key is the number of smaller keys (from the value ranks)
+// plus the number of equal keys before it (a stable 8-bit ranking of value ids
+// per chunk plus running counts), so the records at ranks j*x - 1 are emitted
+// without sorting.  Blocks with more than kLowCardMax values keep their flag
+// for the stable block sort.
+constexpr int kLowCardThreads = 1024, kLowCardItems = 8, kLowCardMax = 256, kLowCardSlots = 512;
+template <int DT>
+__global__ void __launch_bounds__(kLowCardThreads, 1)
+run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t s,
+                          int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry) {
+    using K = typename KeyTraits<DT>::T;
+    static_assert(sizeof(K) == 4, "32-bit keys");
+    constexpr int T = kLowCardThreads, IT = kLowCardItems, CH = T * IT;
+    using Rank = BlockRank<T, IT, 8>;
+    __shared__ typename Rank::Smem rsm;
+    __shared__ unsigned long long slot[kLowCardSlots];  // (1 << 32) | phi, 0 = empty
+    __shared__ uint32_t cnt[kLowCardSlots], id_of[kLowCardSlots];
+    __shared__ uint32_t vals[kLowCardMax], vcnt[kLowCardMax], first[kLowCardMax], running[kLowCardMax];
+    __shared__ int ndistinct, overflow;
+    const int64_t k = blockIdx.x;
+    if (retry[k] == 0) return;  // sorted by the keys-only block sort
+    const uint32_t xx = (uint32_t)x;
+    const int64_t lo = k * m;
+    const int64_t len = lo < n ? imin64(m, n - lo) : 0;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kLowCardSlots; i += T) {
+        slot[i] = 0ull;
+        cnt[i] = 0;
+    }
+    if (tid == 0) {
+        ndistinct = 0;
+        overflow = 0;
+    }
+    __syncthreads();
+    auto hash = [](uint32_t f) {  // murmur3's 32-bit finaliser, top 9 bits
+        f ^= f >> 16;
+        f *= 0x85ebca6bu;
+        f ^= f >> 13;
+        f *= 0xc2b2ae35u;
+        f ^= f >> 16;
+        return f >> (32 - 9);
+    };
+    // slot holding f (inserting it when absent); -1 when the table is full
+    auto find = [&](uint32_t f, bool insert) -> int {
+        const unsigned long long want = (1ull << 32) | f;
+        uint32_t h = hash(f);
+        for (int probe = 0; probe < kLowCardSlots; ++probe, h = (h + 1) & (kLowCardSlots - 1)) {
+            unsigned long long cur = slot[h];
+            if (cur == want) return (int)h;
+            if (cur == 0ull) {
+                if (!insert) return -1;
+                cur = atomicCAS(&slot[h], 0ull, want);
+                if (cur == 0ull) {
+                    if (atomicAdd(&ndistinct, 1) >= kLowCardMax) overflow = 1;
+                    return (int)h;
+                }
+                if (cur == want) return (int)h;
+            }
+        }
+        return -1;
+    };
+    // pass 1: distinct values and their counts
+    for (int64_t e = tid; e < len; e += T) {
+        const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
+        const int h = find(f, true);
+        // lanes holding the same value add their count with one atomic
+        const uint32_t peers = __match_any_sync(__activemask(), f);
+        if (h < 0) overflow = 1;
+        else if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[h], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (overflow || ndistinct > kLowCardMax) return;  // leave the block to the stable sort
+    const int nd = ndistinct;
+    // distinct values in order: value id = number of smaller values
+    if (tid == 0) {
+        int c = 0;
+        for (int i = 0; i < kLowCardSlots; ++i)
+            if (slot[i] != 0ull) {
+                vals[c] = (uint32_t)slot[i];
+                vcnt[c] = cnt[i];
+                id_of[i] = c;
+                ++c;
+            }
+    }
+    __syncthreads();
+    __shared__ uint32_t rank_of[kLowCardMax];
+    if (tid < nd) {
+        uint32_t r = 0;
+        for (int j = 0; j < nd; ++j) r += vals[j] < vals[tid];
+        rank_of[tid] = r;
+    }
+    __syncthreads();
+    if (tid < nd) {
+        const uint32_t r = rank_of[tid];
+        uint32_t below = 0;
+        for (int j = 0; j < nd; ++j) below += rank_of[j] < r ? vcnt[j] : 0u;
+        first[r] = below;
+    }
+    for (int i = tid; i < kLowCardMax; i += T) running[i] = 0;
+    for (int i = tid; i < kLowCardSlots; i += T)
+        if (slot[i] != 0ull) id_of[i] = rank_of[id_of[i]];
+    __syncthreads();
+    // pass 2: in position order, sorted rank = first[id] + earlier equal keys
+    for (int64_t c0 = 0; c0 < len; c0 += CH) {
+        const int clen = (int)imin64(CH, len - c0);
+        uint32_t f[IT], d[IT], rk[IT];
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int sl = striped_slot<T, IT>(i);
+            if (sl < clen) {
+                f[i] = (uint32_t)KeyTraits<DT>::phi(keys[lo + c0 + sl]);
+                const int h = find(f[i], false);  // present: every key was counted
+                d[i] = h >= 0 ? id_of[h] : 0u;
+            } else {
+                d[i] = kLowCardMax - 1;  // after every real key of the chunk
+            }
+        }
+        Rank::rank(rsm, d, rk);
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int sl = striped_slot<T, IT>(i);
+            if (sl < clen) {
+                const uint32_t g1 = first[d[i]] + running[d[i]] + rk[i] + 1;  // < 2^32: block keys
+                if (g1 % xx == 0) {
+                    const int64_t j = g1 / xx;
+                    sphi[k * s + (j - 1)] = (K)f[i];
+                    stag[k * s + (j - 1)] = (uint32_t)(lo + c0 + sl);
+                }
+            }
+        }
+        __syncthreads();
+        for (int dd = tid; dd < kLowCardMax; dd += T) running[dd] += rsm.digit_tot[dd];
+        __syncthreads();
+    }
+    if (tid == 0) retry[k] = 0;  // done
+}
+
 template <typename K>
 __device__ __forceinline__ uint32_t record_digit(K phi, uint32_t tag, int q) {
     return q < 4 ? (tag >> (8 * q)) & 255u : (uint32_t)(phi >> (8 * (q - 4))) & 255u;
@@ -835,6 +977,12 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
         default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
         }
         if (e != cudaSuccess) return e;
+        if (only) {  // blocks of few distinct keys, before the stable sort
+            run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, 0, c.stream>>>(
+                (const K *)c.keys_in, p.n, p.m, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     constexpr int IT = sizeof(K) == 8 ? kRunItems64 : kRunItems32;
     switch (p.run_cl) {
