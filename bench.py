@@ -45,6 +45,11 @@ WORKLOADS = {
     # captures (inputs still larger than L2)
     "uniform_2e26_int32_p4096_random": dict(n=1 << 26, p=4096, sampling=1, s=0, runs=0, pairs=False,
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    # the 2^28 workload's bucket shape (65,536-key buckets on clusters of 8,
+    # count sorts in the occupancy-mask regime) on half the data, for full ncu
+    # captures of the bucket sort
+    "uniform_2e27_int32_p2048_random": dict(n=1 << 27, p=2048, sampling=1, s=0, runs=0, pairs=False,
+                                           make=lambda n, p, seed: gen.uniform(n, p, seed)),
     # the randomized config's shape: 2^26 keys, p = 1024
     "uniform_2e26_int32_p1024_random": dict(n=1 << 26, p=1024, sampling=1, s=0, runs=0, pairs=False,
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),

@@ -75,7 +75,7 @@ template <int DT, int CL, int ITEMS>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
 bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
-    using SS = SegSortKeys<K, CL, ITEMS>;
+    using SS = SegSortKeys<K, CL, ITEMS, false>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t v = blockIdx.x / CL;
     const int64_t cnt = imin64(a.vsize[v], a.cap);
@@ -203,7 +203,9 @@ static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTra
 template <int DT, int CL, int ITEMS>
 static cudaError_t launch_keys(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
     using K = typename KeyTraits<DT>::T;
-    using SS = SegSortKeys<K, CL, ITEMS>;
+    using SS = SegSortKeys<K, CL, ITEMS, false>;
+    // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+    static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024, "two CTAs per SM");
     const size_t smem = SS::smem_bytes();
     auto kern = bucket_keys_kernel<DT, CL, ITEMS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -9,7 +9,7 @@ namespace bsps {
 struct MlpNorm;
 
 // Number of cells of the radix index placed in front of the splitter tree.
-constexpr int kLutBits = 12;
+constexpr int kLutBits = 14;
 constexpr int kLutCells = 1 << kLutBits;
 
 // Routing geometry (Fig. 1 steps 9-11).

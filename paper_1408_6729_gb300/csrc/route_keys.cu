@@ -16,6 +16,7 @@
 namespace bsps {
 
 constexpr int kRkThreads = 1024;
+constexpr int kEarly = 4;  // buckets per thread reserved before the grouping
 constexpr size_t kRkSmemBudget = 200 * 1024;  // splitters in shared memory up to this size
 // keys per thread (fewer with the network's registers in use)
 template <typename K, bool LEARNED = false> constexpr int rk_items() { return sizeof(K) == 8 || LEARNED ? 8 : 16; }
@@ -106,11 +107,11 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
     K kmin = all_ones<K>(), kmax = K(0);
     uint32_t n_mis = 0, n_steps = 0;
 
-    for (int64_t ch = blockIdx.x; ch < a.chunks; ch += gridDim.x) {
+    // chunk keys into registers (key i of a thread is chunk key lidx(i))
+    K kk[IT];
+    auto load_chunk = [&](int64_t ch) {
         const int64_t e0 = ch * CH;
         const int nh = (int)imin64(CH, a.n - e0);
-        // ---- load (registers; key i of a thread is chunk key lidx(i)) ----
-        K kk[IT];
 #pragma unroll
         for (int j = 0; j < IT / V; ++j) {
             const int q = (j * T + tid) * V;
@@ -127,6 +128,12 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
                 for (int e = 0; e < V; ++e) kk[j * V + e] = q + e < nh ? a.keys[e0 + q + e] : K(0);
             }
         }
+    };
+    if ((int64_t)blockIdx.x < a.chunks) load_chunk(blockIdx.x);
+
+    for (int64_t ch = blockIdx.x; ch < a.chunks; ch += gridDim.x) {
+        const int64_t e0 = ch * CH;
+        const int nh = (int)imin64(CH, a.n - e0);
         // ---- classify (Fig. 2 step 9) and rank inside the chunk ----
         uint32_t br[IT];  // bucket << 16 | rank inside the chunk (bucket P: no key)
 #pragma unroll
@@ -182,9 +189,24 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
         }
         __syncthreads();
         uint32_t run = tmp[warp] + wex;
-        for (uint32_t b = b_lo; b < b_hi; ++b) {
+        // the first kEarly of my buckets reserve their runs now, so that the
+        // atomics' round trip overlaps the grouping below
+        uint32_t at_e[kEarly];
+#pragma unroll
+        for (int j = 0; j < kEarly; ++j) {
+            const uint32_t b = b_lo + j;
+            at_e[j] = 0;
+            if (b < b_hi) {
+                const uint32_t c = cnt[b];
+                cnt[b] = run;  // start of the bucket inside the chunk
+                dlt[b] = c;
+                run += c;
+                if (c) at_e[j] = atomicAdd(&a.cursor[b], c);
+            }
+        }
+        for (uint32_t b = b_lo + kEarly; b < b_hi; ++b) {
             const uint32_t c = cnt[b];
-            cnt[b] = run;  // start of the bucket inside the chunk
+            cnt[b] = run;
             dlt[b] = c;
             run += c;
         }
@@ -199,8 +221,20 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
                 stage_b[pos] = (uint16_t)b;
             }
         }
+        // the next chunk's keys load while this one is reserved and written
+        if (ch + gridDim.x < a.chunks) load_chunk(ch + gridDim.x);
         // ---- reserve each bucket's run: one atomic per bucket and chunk ----
-        for (uint32_t g0 = b_lo; g0 < b_hi; g0 += 8) {
+        auto reserved = [&](uint32_t b, uint32_t c, uint32_t at) {
+            if ((uint64_t)at + c > (uint64_t)a.cap) {
+                atomicExch(&a.st->overflow, 1);
+                set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
+            }
+            dlt[b] = at - cnt[b];  // region slot of chunk position s: dlt[b] + s
+        };
+#pragma unroll
+        for (int j = 0; j < kEarly; ++j)
+            if (b_lo + j < b_hi) reserved(b_lo + j, dlt[b_lo + j], at_e[j]);
+        for (uint32_t g0 = b_lo + kEarly; g0 < b_hi; g0 += 8) {
             uint32_t c8[8], at[8];  // eight reservations in flight at a time
 #pragma unroll
             for (int j = 0; j < 8; ++j) c8[j] = g0 + j < b_hi ? dlt[g0 + j] : 0u;
@@ -208,13 +242,7 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
             for (int j = 0; j < 8; ++j) at[j] = c8[j] ? atomicAdd(&a.cursor[g0 + j], c8[j]) : 0u;
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (g0 + j < b_hi) {
-                    if ((uint64_t)at[j] + c8[j] > (uint64_t)a.cap) {
-                        atomicExch(&a.st->overflow, 1);
-                        set_error(a.st, BSPS_ERR_BUCKET_OVERFLOW);
-                    }
-                    dlt[g0 + j] = at[j] - cnt[g0 + j];  // region slot of chunk position s: dlt[b] + s
-                }
+                if (g0 + j < b_hi) reserved(g0 + j, c8[j], at[j]);
         }
         __syncthreads();
         // ---- every bucket's run, contiguously into its region ----

@@ -1,6 +1,11 @@
 // segsort_keys.cuh -- the keys-only bucket sort (Fig. 2 step 12), tuned for
 // throughput: equal keys cannot be told apart, so no ranking needs to be
-// stable and every rank comes from one shared-memory atomic.
+// stable and every rank comes from shared-memory atomics.
+//
+// With MINMAX the split also records every bin's smallest and largest key,
+// which the caller's give_up predicate reads; without it a bin only keeps one
+// of its keys and a flag for any other value, enough to find bins of one
+// distinct key.
 //
 // A cluster of CL CTAs (512 threads, two per SM) sorts one sub-bucket whose
 // keys lie in [lo, hi] (bounds from the splitters).  Each CTA loads its share
@@ -11,10 +16,11 @@
 // to one CTA, and each CTA copies its stage, bin run by bin run, into the
 // owners' receive buffers.  Each CTA then counting-sorts what it received on
 // up to kCountBits further bits.  When a count bin spans at most 32 values,
-// two occupancy masks per bin record which values occur at least once and at
-// least twice; in a bin where no value occurs three times a key's place is a
-// sum of popcounts of the masks below its value plus its occurrence index.
-// Keys of other bins are placed by comparison.  A bin too large for one CTA,
+// three occupancy masks per bin record which values occur at least once,
+// twice and three times, and later occurrences are only counted; in a bin
+// where no value occurs four times a key's place is the bin start plus the
+// popcounts of the masks below its value plus its occurrence index.  Keys of
+// other bins are placed by comparison.  A bin too large for one CTA,
 // or count bins longer than kBinMax that need comparisons, make the cluster
 // give the sub-bucket back (returns false) to the stable cluster sort of
 // segsort.cuh.
@@ -24,7 +30,21 @@
 
 namespace bsps {
 
-template <typename K, int CL, int ITEMS>
+// address of a shared-memory location of this CTA in CTA `rank` of the
+// cluster (shared::cluster window), and a store through such an address
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t cta_addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(cta_addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, uint64_t v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+template <typename K, int CL, int ITEMS, bool MINMAX = true>
 struct SegSortKeys {
     static constexpr int T = 512;
     static constexpr int V = 16 / (int)sizeof(K);     // keys per 16-byte load
@@ -38,19 +58,22 @@ struct SegSortKeys {
 
     struct Smem {
         uint32_t cnt[R];     // my keys per split bin (read by the other CTAs)
-        K bmin[R], bmax[R];  // my smallest / largest key per split bin (read by the others)
-        uint32_t lbase[R];   // start of the bin in my stage
+        K bmin[R];           // my smallest key per split bin, or (without MINMAX) any of them
+        K bmax[MINMAX ? R : 1];  // my largest key per split bin (read by the others)
+        uint32_t lbase[R];   // start of the bin in my stage; then where the exchange sends it
         uint32_t start[R];   // first output position of the bin
         uint32_t pre[R];     // keys of the bin held by lower-ranked CTAs
-        uint32_t dst[R];     // start of the bin in its owner's receive buffer
+        uint32_t dst[R];     // start of the bin in its owner's receive buffer; then start - dst
         int32_t owner[R];    // -1: bin with one distinct key (or none)
         uint32_t recv[8], own_base[8], ofirst[8], olast[8];
         uint32_t tmp[40];
         uint32_t heavy;      // keys in bins the caller's give_up predicate marks
+        uint8_t diff[MINMAX ? 1 : R];  // without MINMAX: my bin holds a key other than bmin
     };
-    // the count histogram and the two masks (one word per bin) live in the
-    // receive buffer, which is free by then; the buffer is sized for both
-    static constexpr int kM1 = kCountBins + 4, kM2 = kM1 + kCountBins, kScratchWords = kM2 + kCountBins;
+    // the count histogram and the three masks (one word per bin) live in the
+    // receive buffer, which is free by then; the buffer is sized for all four
+    static constexpr int kM1 = kCountBins + 4, kM2 = kM1 + kCountBins, kM3 = kM2 + kCountBins,
+                         kScratchWords = kM3 + kCountBins;
     static constexpr size_t kBufBytes =
         ((size_t)CAP * sizeof(K) > (size_t)kScratchWords * 4 ? (size_t)CAP * sizeof(K) : (size_t)kScratchWords * 4);
     static constexpr size_t smem_bytes() {
@@ -161,48 +184,91 @@ struct SegSortKeys {
         const int shift = bits - nbb;
         const int nb = 1 << nbb;
         const bool masks = shift > 0 && shift <= kMaskBits;
-        uint32_t *chist = scr, *m1 = scr + kM1, *m2 = scr + kM2;
+        uint32_t *chist = scr, *m1 = scr + kM1, *m2 = scr + kM2, *m3 = scr + kM3;
         __syncthreads();  // scr may still be read by the caller
         for (int b = threadIdx.x; b < nb; b += T) chist[b] = 0;
         if (masks)
-            for (int b = threadIdx.x; b < nb; b += T) m1[b] = m2[b] = 0;
+            for (int b = threadIdx.x; b < nb; b += T) m1[b] = m2[b] = m3[b] = 0;
         __syncthreads();
-        // r: rank inside the count bin (bits 0..27), occurrence of the value (28..29)
+        // without masks r is the rank inside the count bin.  With masks it is
+        // the occurrence of the value (bits 28..29: first, second, third,
+        // later) and, for later ones, their rank among the bin's later
+        // occurrences (bits 0..27), which chist counts.
         uint32_t r[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if (valid(i)) {
                 const uint32_t bb = bin(k[i], lo, shift, nb - 1);
-                r[i] = atomicAdd(&chist[bb], 1u);
                 if (masks) {
                     const uint32_t bit = 1u << (uint32_t)((k[i] - lo) & (K)31);
-                    if (atomicOr(&m1[bb], bit) & bit) r[i] |= (atomicOr(&m2[bb], bit) & bit) ? 2u << 28 : 1u << 28;
+                    uint32_t o = 0;
+                    if (atomicOr(&m1[bb], bit) & bit) {
+                        o = 1u << 28;
+                        if (atomicOr(&m2[bb], bit) & bit) {
+                            o = 2u << 28;
+                            if (atomicOr(&m3[bb], bit) & bit) o = 3u << 28 | atomicAdd(&chist[bb], 1u);
+                        }
+                    }
+                    r[i] = o;
+                } else {
+                    r[i] = atomicAdd(&chist[bb], 1u);
                 }
             }
         __syncthreads();
-        if (!scan_bins(chist, nb, sm.tmp, shift > kMaskBits)) return false;
-        // keys alone in their bin, or in a bin whose values occur at most
-        // twice, go to their final place; the others wait at bin start + rank
+        if (masks) {  // bin length: one key per mask bit, plus the later occurrences
+            for (int b = threadIdx.x; b < nb; b += T) chist[b] += __popc(m1[b]) + __popc(m2[b]) + __popc(m3[b]);
+            __syncthreads();
+        }
+        if (!scan_bins(chist, nb, sm.tmp, !masks && shift > 0)) return false;
+        constexpr uint32_t kStart = 0x7fffffffu;  // bin start; bit 31: a value repeats
         bool cmp = false;
+        if (masks) {
+            for (int b = threadIdx.x; b < nb; b += T)
+                if (m2[b]) chist[b] |= ~kStart;
+            __syncthreads();
+            // In a bin of distinct values a key's place follows from the
+            // first mask alone.  In others it is final when no value occurs
+            // four times (keys of smaller values + occurrence); otherwise the
+            // key waits in a distinct slot of the bin (first occurrences, then
+            // second, third and later ones) for the comparisons below.
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (valid(i)) {
-                const uint32_t bb = bin(k[i], lo, shift, nb - 1);
-                const uint32_t b0 = chist[bb], len = chist[bb + 1] - b0;
-                uint32_t pos = b0 + (r[i] & 0x0fffffffu);
-                bool fin = shift == 0 || len == 1;
-                if (masks && !fin) {
-                    const uint32_t w1 = m1[bb], w2 = m2[bb];
-                    if ((uint32_t)(__popc(w1) + __popc(w2)) == len) {
-                        const uint32_t below = (1u << (uint32_t)((k[i] - lo) & (K)31)) - 1u;
-                        pos = b0 + __popc(w1 & below) + __popc(w2 & below) + (r[i] >> 28);
-                        fin = true;
+            for (int i = 0; i < ITEMS; ++i)
+                if (valid(i)) {
+                    const uint32_t bb = bin(k[i], lo, shift, nb - 1);
+                    const uint32_t h = chist[bb], b0 = h & kStart;
+                    const uint32_t below = (1u << (uint32_t)((k[i] - lo) & (K)31)) - 1u;
+                    const uint32_t w1 = m1[bb];
+                    uint32_t pos = b0 + __popc(w1 & below);
+                    bool fin = true;
+                    if (h & ~kStart) {
+                        const uint32_t len = (chist[bb + 1] & kStart) - b0;
+                        const uint32_t w2 = m2[bb], w3 = m3[bb], occ = r[i] >> 28;
+                        const uint32_t c1 = __popc(w1), c12 = c1 + __popc(w2), c123 = c12 + __popc(w3);
+                        const uint32_t l2 = __popc(w2 & below), l3 = __popc(w3 & below);
+                        fin = c123 == len;
+                        if (fin) pos += l2 + l3 + occ;
+                        else if (occ == 1) pos = b0 + c1 + l2;
+                        else if (occ == 2) pos = b0 + c12 + l3;
+                        else if (occ == 3) pos = b0 + c123 + (r[i] & 0x0fffffffu);
                     }
+                    out[pos] = k[i];
+                    r[i] = fin ? 0xffffffffu : pos;
+                    cmp |= !fin;
                 }
-                out[pos] = k[i];
-                r[i] = fin ? 0xffffffffu : pos;
-                cmp |= !fin;
-            }
+        } else {
+            // keys alone in their bin go to their final place, the others
+            // wait at bin start + rank
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (valid(i)) {
+                    const uint32_t bb = bin(k[i], lo, shift, nb - 1);
+                    const uint32_t b0 = chist[bb], pos = b0 + r[i];
+                    const bool fin = shift == 0 || chist[bb + 1] - b0 == 1;
+                    out[pos] = k[i];
+                    r[i] = fin ? 0xffffffffu : pos;
+                    cmp |= !fin;
+                }
+        }
         if (!__syncthreads_or(cmp)) return true;
         // place = bin start + keys of the bin below k + equal keys stored before it
         bool too_long = false;
@@ -210,7 +276,7 @@ struct SegSortKeys {
         for (int i = 0; i < ITEMS; ++i)
             if (valid(i) && r[i] != 0xffffffffu) {
                 const uint32_t bb = bin(k[i], lo, shift, nb - 1);
-                const uint32_t b0 = chist[bb], b1 = chist[bb + 1], self = r[i];
+                const uint32_t b0 = chist[bb] & kStart, b1 = chist[bb + 1] & kStart, self = r[i];
                 if (b1 - b0 > kBinMax) {
                     too_long = true;
                 } else {
@@ -282,7 +348,8 @@ struct SegSortKeys {
             if (tid < R) {
                 sm.cnt[tid] = 0;
                 sm.bmin[tid] = all_ones<K>();
-                sm.bmax[tid] = 0;
+                if constexpr (MINMAX) sm.bmax[tid] = 0;
+                else sm.diff[tid] = 0;
             }
             if (tid < 8) {
                 sm.recv[tid] = 0;
@@ -298,7 +365,9 @@ struct SegSortKeys {
                 if (mine(i)) {
                     const uint32_t d = bin(k[i], lo, shift, nbins - 1);
                     r[i] = atomicAdd(&sm.cnt[d], 1u);
-                    atomic_min_max(&sm.bmin[d], &sm.bmax[d], k[i]);
+                    if constexpr (MINMAX) atomic_min_max(&sm.bmin[d], &sm.bmax[d], k[i]);
+                    else sm.bmin[d] = k[i];  // any key of the bin will do
+
                 }
             __syncthreads();
             if (tid < R) sm.lbase[tid] = sm.cnt[tid];
@@ -307,25 +376,40 @@ struct SegSortKeys {
             // group my keys by bin in the stage
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i)
-                if (mine(i)) stage[sm.lbase[bin(k[i], lo, shift, nbins - 1)] + r[i]] = k[i];
+                if (mine(i)) {
+                    const uint32_t d = bin(k[i], lo, shift, nbins - 1);
+                    stage[sm.lbase[d] + r[i]] = k[i];
+                    if constexpr (!MINMAX)
+                        if (k[i] != sm.bmin[d]) sm.diff[d] = 1;
+                }
             cluster.sync();
             // every CTA derives the same global bin layout from all counts
             uint32_t tot = 0, pre = 0;
             K gmin = all_ones<K>(), gmax = 0;
+            bool one = true;  // without MINMAX: every key of the bin equals gmin
             if (tid < nbins) {
 #pragma unroll
                 for (int q = 0; q < CL; ++q) {
                     const uint32_t t = *cluster.map_shared_rank(&sm.cnt[tid], q);
                     const K x = *cluster.map_shared_rank(&sm.bmin[tid], q);
-                    const K y = *cluster.map_shared_rank(&sm.bmax[tid], q);
+                    if constexpr (MINMAX) {
+                        const K y = *cluster.map_shared_rank(&sm.bmax[tid], q);
+                        gmin = x < gmin ? x : gmin;
+                        gmax = y > gmax ? y : gmax;
+                    } else {
+                        const uint8_t df = *cluster.map_shared_rank(&sm.diff[tid], q);
+                        if (t) {
+                            one &= df == 0 && (tot == 0 || x == gmin);
+                            gmin = x;
+                        }
+                    }
                     pre += q < c ? t : 0u;
                     tot += t;
-                    gmin = x < gmin ? x : gmin;
-                    gmax = y > gmax ? y : gmax;
                 }
             }
-            const bool flat = tot == 0 || gmin == gmax;
-            if (!flat && give_up(gmin, gmax)) atomicAdd(&sm.heavy, tot);
+            const bool flat = tot == 0 || (MINMAX ? gmin == gmax : one);
+            if constexpr (MINMAX)
+                if (!flat && give_up(gmin, gmax)) atomicAdd(&sm.heavy, tot);
             if (tid < R) {
                 sm.pre[tid] = pre;
                 sm.start[tid] = tot;
@@ -350,7 +434,20 @@ struct SegSortKeys {
                 sm.owner[tid] = t;
             }
             __syncthreads();
-            if (tid < R && sm.owner[tid] >= 0) sm.dst[tid] -= sm.own_base[sm.owner[tid]];
+            if (tid < R) {
+                const int t = sm.owner[tid];
+                const uint32_t d0 = t >= 0 ? sm.dst[tid] - sm.own_base[t] : 0u;
+                // key j of my stage goes to slot x + j of its owner's buffer, or
+                // (one-key bins) to output position x + j; received key j of a
+                // bin goes to output position dst[d] + j (modular arithmetic).
+                // lbase[d] becomes the shared::cluster address of slot x in the
+                // owner's buffer (even: K-aligned), or 2x + 1 (x < 2^31 here).
+                const uint32_t x = (t >= 0 ? d0 : sm.start[tid]) + sm.pre[tid] - sm.lbase[tid];
+                sm.lbase[tid] = t >= 0 ? cluster_addr((uint32_t)__cvta_generic_to_shared(buf), (uint32_t)t) +
+                                             x * (uint32_t)sizeof(K)
+                                       : x << 1 | 1u;
+                sm.dst[tid] = sm.start[tid] - d0;
+            }
             bool bail = (int64_t)sm.heavy * 4 > cnt;
 #pragma unroll
             for (int q = 0; q < CL; ++q) bail |= sm.recv[q] > (uint32_t)CAP;
@@ -362,11 +459,9 @@ struct SegSortKeys {
             // exchange: stage runs to their owners, one-key bins straight out
             for (int j = tid; j < mycnt; j += T) {
                 const K x = stage[j];
-                const uint32_t d = bin(x, lo, shift, nbins - 1);
-                const uint32_t at = sm.pre[d] + ((uint32_t)j - sm.lbase[d]);
-                const int t = sm.owner[d];
-                if (t < 0) emit(sm.start[d] + at, x);
-                else cluster.map_shared_rank(buf, t)[sm.dst[d] + at] = x;
+                const uint32_t at = sm.lbase[bin(x, lo, shift, nbins - 1)];
+                if (at & 1u) emit((at >> 1) + (uint32_t)j, x);
+                else st_cluster(at + (uint32_t)j * (uint32_t)sizeof(K), x);
             }
             cluster.sync();
             const int got = (int)sm.recv[c];
@@ -383,10 +478,17 @@ struct SegSortKeys {
             // the others emit is rewritten, identically, by the stable sort
             if (!count_sort(sm, k, received, llo, bit_length<K>(lhi - llo), stage, reinterpret_cast<uint32_t *>(buf)))
                 return false;
-            for (int j = tid; j < got; j += T) {
-                const K x = stage[j];
-                const uint32_t d = bin(x, lo, shift, nbins - 1);
-                emit(sm.start[d] + ((uint32_t)j - sm.dst[d]), x);
+            // with no one-key bin between the owned bins (dst[d] is then the
+            // same for all of them) the received keys fill one output range
+            if (sm.dst[first] == sm.dst[last]) {
+                const uint32_t o = sm.dst[first];
+                for (int j = tid; j < got; j += T) emit(o + (uint32_t)j, stage[j]);
+            } else {
+                for (int j = tid; j < got; j += T) {
+                    const K x = stage[j];
+                    const uint32_t d = bin(x, lo, shift, nbins - 1);
+                    emit(sm.dst[d] + (uint32_t)j, x);
+                }
             }
             return true;
         }

@@ -252,3 +252,24 @@ def test_block_sort_float_total_order_and_duplicates(runs):
     ref = ref_sort(keys, p, 64, runs, oracle.REGULAR, 0)
     gpu = run_gpu(keys, p, 64, runs, oracle.REGULAR, 0)
     assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("dt", ["int32", "float64"])
+@pytest.mark.parametrize("span_log2", [19, 20, 21, 23, 25])
+def test_bucket_sort_repeat_rates(dt, span_log2):
+    """Keys-only bucket sort of 65536-key buckets (clusters of 8) whose values
+    repeat at different rates: keys uniform on 2^span consecutive values.  This
+    walks a cluster CTA's count sort through its regimes: one value per count
+    bin (2^19), occupancy masks with values seen up to three times and bins
+    where a value occurs four times or more, placed by comparison (2^20, 2^21),
+    the sparse regime of the 2^28 workload (2^23), and comparison only (2^25).
+    float64 keys 2^20 + j 2^-32 are consecutive doubles, so their phi values
+    repeat at the same rates."""
+    n, p = 1 << 20, 16
+    rng = np.random.default_rng(span_log2)
+    j = rng.integers(0, 1 << span_log2, n)
+    keys = j.astype(np.int32) if dt == "int32" else 2.0**20 + j * 2.0**-32
+    ref = ref_sort(keys, p, 0, 0, oracle.RANDOM, 5)
+    gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 5)
+    assert gpu.plan.bucket_cluster == 8
+    assert_same(gpu, ref)
