@@ -220,7 +220,7 @@ static int kernels_per_call(const Plan &pl) {
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
-    k += pl.pairs ? 2 : 3;                       // cluster bucket sort tiers, out-of-core bucket sort
+    k += 3;                                      // copy or keys-only tier, cluster sort, out-of-core sort
     if (pl.classify == BSPS_LEARNED) k += 4;     // training set, spline start, features, output-layer steps
     return k;
 }

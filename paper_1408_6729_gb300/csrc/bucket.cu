@@ -3,9 +3,10 @@
 // to the bucket's place in the output.  Each sub-bucket is sorted on chip by
 // one thread-block cluster, in up to three tiers:
 //   1. keys only: the throughput sort of segsort_keys.cuh (unstable ranks,
-//      which equal keys cannot reveal);
-//   2. with payloads, or what tier 1 gives back: the stable cluster sort of
-//      segsort.cuh;
+//      which equal keys cannot reveal); with payloads: sub-buckets of one key
+//      value are copied as they stand;
+//   2. the other sub-buckets with payloads, or what tier 1 gives back: the
+//      stable cluster sort of segsort.cuh over a list;
 //   3. sub-buckets larger than a cluster's shared memory: an out-of-core
 //      radix sort in global memory.
 #include "kernels.cuh"
@@ -69,6 +70,35 @@ bucket_sort_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     }
 }
 
+// With payloads, before the cluster sort: a sub-bucket between two splitters
+// of equal phi holds one key value, and routing kept its keys in input order,
+// which is their sorted order under the position tie-break (Sec. 5.1.1); it is
+// copied out as it stands.  Every other non-empty sub-bucket goes on the list
+// the cluster sort then works through.
+constexpr int kCopyThreads = 512;
+template <int DT, bool PAIRS>
+__global__ void __launch_bounds__(kCopyThreads) bucket_copy_kernel(const BucketArgs<typename KeyTraits<DT>::T> a,
+                                                                  uint32_t *list, int32_t *list_count) {
+    using K = typename KeyTraits<DT>::T;
+    for (int64_t v = blockIdx.x; v < a.P; v += gridDim.x) {
+        const int64_t cnt = imin64(a.vsize[v], a.cap);
+        if (cnt == 0) continue;
+        if (v > 0 && v < a.P - 1 && a.vphi[v - 1] == a.vphi[v]) {
+            const K x = KeyTraits<DT>::inv(a.vphi[v]);
+            K *out_k = a.out_keys + a.voff[v];
+            uint32_t *out_v = a.out_vals + a.voff[v];
+            const uint32_t *vsrc = a.reg_vals + v * a.cap;
+#pragma unroll 8
+            for (int64_t e = threadIdx.x; e < cnt; e += kCopyThreads) {
+                out_k[e] = x;
+                if constexpr (PAIRS) out_v[e] = vsrc[e];
+            }
+        } else if (threadIdx.x == 0) {
+            list[atomicAdd(list_count, 1)] = (uint32_t)v;
+        }
+    }
+}
+
 // Tier 1 (keys only): one cluster per sub-bucket; its bounds are the two
 // splitters around it (the smallest and largest key for the end buckets).
 template <int DT, int CL, int ITEMS>
@@ -83,6 +113,14 @@ bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     const K lo = v > 0 ? a.vphi[v - 1] : (K)~a.st->ext_min_inv;
     const K hi = v < a.P - 1 ? a.vphi[v] : (K)a.st->ext_max;
     K *out_k = a.out_keys + a.voff[v];
+    if (lo == hi) {  // one key value: nothing to read
+        const K x = KeyTraits<DT>::inv(lo);
+        const int64_t share = (cnt + CL - 1) / CL, e0 = (int64_t)(blockIdx.x % CL) * share;
+        const int64_t e1 = imin64(cnt, e0 + share);
+#pragma unroll 4
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) out_k[e] = x;
+        return;
+    }
     auto emit = [&](uint32_t pos, K key) { out_k[pos] = KeyTraits<DT>::inv(key); };
     if (!SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
         if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
@@ -195,7 +233,13 @@ static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTra
     auto kern = bucket_sort_kernel<DT, PAIRS, CL, ITEMS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t clusters = listed ? imin64(16, c.pl.P) : c.pl.P;
+    int64_t clusters = c.pl.P;
+    if (listed) {  // as many clusters as run at once (one CTA per SM), at least 16
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        clusters = imin64(c.pl.P, imax64(16, sms / CL));
+    }
     kern<<<(unsigned)(clusters * CL), 1024, smem, c.stream>>>(a);
     return cudaGetLastError();
 }
@@ -250,11 +294,21 @@ template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
         a.only_count = &c.ly.status->retry_count;
         e = launch_cluster<DT, false, 8, IT>(c, a, true);
     } else {
+        // one-value sub-buckets are copied; the cluster sort takes the list of the others
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        bucket_copy_kernel<DT, PAIRS><<<(unsigned)imin64(c.pl.P, 4 * (int64_t)sms), kCopyThreads, 0, c.stream>>>(
+            a, c.ly.retry_list, &c.ly.status->retry_count);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.only = c.ly.retry_list;
+        a.only_count = &c.ly.status->retry_count;
         switch (c.pl.bucket_cl) {
-        case 1: e = launch_cluster<DT, PAIRS, 1, IT>(c, a, false); break;
-        case 2: e = launch_cluster<DT, PAIRS, 2, IT>(c, a, false); break;
-        case 4: e = launch_cluster<DT, PAIRS, 4, IT>(c, a, false); break;
-        case 8: e = launch_cluster<DT, PAIRS, 8, IT>(c, a, false); break;
+        case 1: e = launch_cluster<DT, PAIRS, 1, IT>(c, a, true); break;
+        case 2: e = launch_cluster<DT, PAIRS, 2, IT>(c, a, true); break;
+        case 4: e = launch_cluster<DT, PAIRS, 4, IT>(c, a, true); break;
+        case 8: e = launch_cluster<DT, PAIRS, 8, IT>(c, a, true); break;
         default: return cudaErrorInvalidValue;
         }
     }

@@ -63,7 +63,7 @@ struct DevStatus {
     unsigned long long correction_steps;
     uint32_t tile_counter;      // dynamic tile ticket of the routing kernel
     uint32_t run_too_big;       // a block of the regular sample did not fit on chip
-    int32_t retry_count;        // sub-buckets the keys-only sort gave back
+    int32_t retry_count;        // sub-buckets for the stable cluster sort (keys only: given back)
     uint32_t pad_[5];
     unsigned long long ext_min_inv;  // ~(smallest phi of bucket 0); 0 = none seen
     unsigned long long ext_max;      // largest phi of the last bucket

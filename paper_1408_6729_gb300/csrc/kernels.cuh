@@ -84,7 +84,7 @@ struct Layout {
     uint16_t *ids;          // tiles * kRouteTile sub-bucket ids (routing scratch)
     uint32_t *cursor;       // P keys routed per sub-bucket
     uint32_t *retry_flag;   // P: the keys-only sort gave the sub-bucket back
-    uint32_t *retry_list;   // P
+    uint32_t *retry_list;   // P: sub-buckets for the stable cluster sort
     uint32_t *run_retry;    // R: blocks the keys-only block sort gave back
     // learned classifier (classify == BSPS_LEARNED)
     float *mlp_params;                   // 1153

@@ -151,37 +151,40 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 // ---------------------------------------------------------------------------
 // Blocks of few distinct keys (regular sampling, 32-bit keys): a block's
 // sorted order by (phi, tag) is its distinct values in order, each repeated in
-// position order.  One CTA counts the values in a shared-memory hash table,
-// ranks the distinct values, and then walks the block in position order: the
-// sorted rank of a key is the number of smaller keys (from the value ranks)
-// plus the number of equal keys before it (a stable 8-bit ranking of value ids
-// per chunk plus running counts), so the records at ranks j*x - 1 are emitted
+// position order.  One CTA finds the values with a shared-memory hash table;
+// warp w of the CTA owns the w-th of 32 contiguous segments of the block and
+// counts the values in it.  From the counts come the distinct values' sorted
+// starts and, per warp, the keys of each value in earlier segments.  Every
+// warp then walks its segment again in position order: the sorted rank of a
+// key is the start of its value, plus that value's keys in earlier segments,
+// plus its earlier occurrences in this segment (a running count and the lanes
+// of the same value below it).  The records at ranks j*x - 1 are emitted
 // without sorting.  Blocks with more than kLowCardMax values keep their flag
 // for the stable block sort.
-constexpr int kLowCardThreads = 1024, kLowCardItems = 8, kLowCardMax = 256, kLowCardSlots = 512;
+constexpr int kLowCardThreads = 1024, kLowCardMax = 256, kLowCardSlots = 512;
+constexpr int kLowCardWarps = kLowCardThreads / 32;
+constexpr size_t kLowCardSmem = sizeof(uint32_t) * kLowCardWarps * kLowCardSlots;  // per-warp counts
 template <int DT>
 __global__ void __launch_bounds__(kLowCardThreads, 1)
 run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t s,
                           int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry) {
     using K = typename KeyTraits<DT>::T;
     static_assert(sizeof(K) == 4, "32-bit keys");
-    constexpr int T = kLowCardThreads, IT = kLowCardItems, CH = T * IT;
-    using Rank = BlockRank<T, IT, 8>;
-    __shared__ typename Rank::Smem rsm;
-    __shared__ unsigned long long slot[kLowCardSlots];  // (1 << 32) | phi, 0 = empty
-    __shared__ uint32_t cnt[kLowCardSlots], id_of[kLowCardSlots];
-    __shared__ uint32_t vals[kLowCardMax], vcnt[kLowCardMax], first[kLowCardMax], running[kLowCardMax];
+    constexpr int T = kLowCardThreads, W = kLowCardWarps, NS = kLowCardSlots;
+    extern __shared__ __align__(16) uint32_t wcnt[];       // [W][NS]: keys per slot in warp w's segment
+    __shared__ unsigned long long slot[NS];                 // (1 << 32) | phi, 0 = empty
+    __shared__ uint32_t start[NS];                          // sorted start of the slot's value
+    __shared__ uint32_t vals[kLowCardMax], sid[kLowCardMax], rank_of[kLowCardMax], tot_sorted[kLowCardMax];
+    __shared__ uint32_t tmp[W + 1];
     __shared__ int ndistinct, overflow;
     const int64_t k = blockIdx.x;
     if (retry[k] == 0) return;  // sorted by the keys-only block sort
     const uint32_t xx = (uint32_t)x;
     const int64_t lo = k * m;
     const int64_t len = lo < n ? imin64(m, n - lo) : 0;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kLowCardSlots; i += T) {
-        slot[i] = 0ull;
-        cnt[i] = 0;
-    }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < NS; i += T) slot[i] = 0ull;
+    for (int i = tid; i < W * NS; i += T) wcnt[i] = 0;
     if (tid == 0) {
         ndistinct = 0;
         overflow = 0;
@@ -195,11 +198,12 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
         f ^= f >> 16;
         return f >> (32 - 9);
     };
+    static_assert(NS == 512, "9-bit hash");
     // slot holding f (inserting it when absent); -1 when the table is full
     auto find = [&](uint32_t f, bool insert) -> int {
         const unsigned long long want = (1ull << 32) | f;
         uint32_t h = hash(f);
-        for (int probe = 0; probe < kLowCardSlots; ++probe, h = (h + 1) & (kLowCardSlots - 1)) {
+        for (int probe = 0; probe < NS; ++probe, h = (h + 1) & (NS - 1)) {
             unsigned long long cur = slot[h];
             if (cur == want) return (int)h;
             if (cur == 0ull) {
@@ -214,78 +218,93 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
         }
         return -1;
     };
-    // pass 1: distinct values and their counts
-    for (int64_t e = tid; e < len; e += T) {
-        const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
-        const int h = find(f, true);
-        // lanes holding the same value add their count with one atomic
-        const uint32_t peers = __match_any_sync(__activemask(), f);
-        if (h < 0) overflow = 1;
-        else if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[h], (uint32_t)__popc(peers));
+    // warp w's segment of the block: [seg0, seg1), whole steps of 32 keys
+    const int64_t seg = ((len + W - 1) / W + 31) / 32 * 32;
+    const int64_t seg0 = imin64(len, warp * seg), seg1 = imin64(len, seg0 + seg);
+    uint32_t *mine = wcnt + warp * NS;
+    // pass 1: distinct values, and their keys per segment
+    for (int64_t e0 = seg0; e0 < seg1; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool ok = e < seg1;
+        const uint32_t act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
+            const int h = find(f, true);
+            const uint32_t peers = __match_any_sync(act, f);
+            if (h < 0) overflow = 1;
+            else if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);  // this warp's own counts
+        }
     }
     __syncthreads();
     if (overflow || ndistinct > kLowCardMax) return;  // leave the block to the stable sort
     const int nd = ndistinct;
-    // distinct values in order: value id = number of smaller values
-    if (tid == 0) {
-        int c = 0;
-        for (int i = 0; i < kLowCardSlots; ++i)
-            if (slot[i] != 0ull) {
-                vals[c] = (uint32_t)slot[i];
-                vcnt[c] = cnt[i];
-                id_of[i] = c;
-                ++c;
-            }
+    // the distinct values, compacted in slot order (ballots over the slots)
+    if (tid < NS) {
+        const uint32_t b = __ballot_sync(0xffffffffu, slot[tid] != 0ull);
+        if (lane == 0) tmp[warp] = (uint32_t)__popc(b);
     }
     __syncthreads();
-    __shared__ uint32_t rank_of[kLowCardMax];
+    if (tid < NS) {
+        const bool occ = slot[tid] != 0ull;
+        uint32_t c = (uint32_t)__popc(__ballot_sync(0xffffffffu, occ) & lanemask_lt());
+        for (int w = 0; w < warp; ++w) c += tmp[w];
+        if (occ) {
+            vals[c] = (uint32_t)slot[tid];
+            sid[c] = (uint32_t)tid;
+        }
+    }
+    __syncthreads();
+    // value rank = number of smaller values; per value its total and, per
+    // warp, its keys in earlier segments (in place of the counts)
     if (tid < nd) {
         uint32_t r = 0;
-        for (int j = 0; j < nd; ++j) r += vals[j] < vals[tid];
+        const uint32_t v = vals[tid];
+        for (int j = 0; j < nd; ++j) r += vals[j] < v;
         rank_of[tid] = r;
+        const uint32_t h = sid[tid];
+        uint32_t acc = 0;
+        for (int w = 0; w < W; ++w) {
+            const uint32_t b = wcnt[w * NS + h];
+            wcnt[w * NS + h] = acc;
+            acc += b;
+        }
+        tot_sorted[r] = acc;
+    }
+    __syncthreads();
+    // first sorted position of every value: exclusive scan in rank order
+    uint32_t ex = 0;
+    if (tid < kLowCardMax) {
+        uint32_t wt;
+        ex = warp_excl_scan(tid < nd ? tot_sorted[tid] : 0u, &wt);
+        if (lane == 31) tmp[warp] = wt;
     }
     __syncthreads();
     if (tid < nd) {
-        const uint32_t r = rank_of[tid];
-        uint32_t below = 0;
-        for (int j = 0; j < nd; ++j) below += rank_of[j] < r ? vcnt[j] : 0u;
-        first[r] = below;
+        for (int w = 0; w < warp; ++w) ex += tmp[w];
+        tot_sorted[tid] = ex;
     }
-    for (int i = tid; i < kLowCardMax; i += T) running[i] = 0;
-    for (int i = tid; i < kLowCardSlots; i += T)
-        if (slot[i] != 0ull) id_of[i] = rank_of[id_of[i]];
     __syncthreads();
-    // pass 2: in position order, sorted rank = first[id] + earlier equal keys
-    for (int64_t c0 = 0; c0 < len; c0 += CH) {
-        const int clen = (int)imin64(CH, len - c0);
-        uint32_t f[IT], d[IT], rk[IT];
-#pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            const int sl = striped_slot<T, IT>(i);
-            if (sl < clen) {
-                f[i] = (uint32_t)KeyTraits<DT>::phi(keys[lo + c0 + sl]);
-                const int h = find(f[i], false);  // present: every key was counted
-                d[i] = h >= 0 ? id_of[h] : 0u;
-            } else {
-                d[i] = kLowCardMax - 1;  // after every real key of the chunk
+    if (tid < nd) start[sid[tid]] = tot_sorted[rank_of[tid]];
+    __syncthreads();
+    // pass 2: in position order, sorted rank = start + earlier segments + earlier here
+    for (int64_t e0 = seg0; e0 < seg1; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool ok = e < seg1;
+        const uint32_t act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
+            const int h = max(0, find(f, false));  // present: every key was counted
+            const uint32_t peers = __match_any_sync(act, f);
+            const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
+            __syncwarp(act);
+            if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
+            if (g1 % xx == 0) {
+                const int64_t j = g1 / xx;
+                sphi[k * s + (j - 1)] = (K)f;
+                stag[k * s + (j - 1)] = (uint32_t)(lo + e);
             }
         }
-        Rank::rank(rsm, d, rk);
-#pragma unroll
-        for (int i = 0; i < IT; ++i) {
-            const int sl = striped_slot<T, IT>(i);
-            if (sl < clen) {
-                const uint32_t g1 = first[d[i]] + running[d[i]] + rk[i] + 1;  // < 2^32: block keys
-                if (g1 % xx == 0) {
-                    const int64_t j = g1 / xx;
-                    sphi[k * s + (j - 1)] = (K)f[i];
-                    stag[k * s + (j - 1)] = (uint32_t)(lo + c0 + sl);
-                }
-            }
-        }
-        __syncthreads();
-        for (int dd = tid; dd < kLowCardMax; dd += T) running[dd] += rsm.digit_tot[dd];
-        __syncthreads();
+        __syncwarp();
     }
     if (tid == 0) retry[k] = 0;  // done
 }
@@ -978,7 +997,10 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
         }
         if (e != cudaSuccess) return e;
         if (only) {  // blocks of few distinct keys, before the stable sort
-            run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, 0, c.stream>>>(
+            e = cudaFuncSetAttribute(run_sample_lowcard_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLowCardSmem);
+            if (e != cudaSuccess) return e;
+            run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, kLowCardSmem, c.stream>>>(
                 (const K *)c.keys_in, p.n, p.m, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
