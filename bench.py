@@ -79,14 +79,16 @@ PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "
                 ("route", True): "route_kernel", ("bucket_sort", True): "bucket_sort_kernel"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
-# ncu capture (profiles/*.md), valid while the kernel source is unchanged.
-# (profiles/*_uniform_2e26_int32_p4096_random.md: 2^26-key captures; both
-# kernels stream every key once, so bytes per key carry over to 2^28)
-NCU_TRAFFIC = {"route_keys_kernel": ((270.544128e6 + 220.683520e6) / (1 << 26), "54aa1426cb9026f3"),
-               "bucket_keys_kernel": ((269.037568e6 + 218.690304e6) / (1 << 26), "e5632899d558dff5")}
+# ncu capture (profiles/*.md), valid while the kernel source is unchanged:
+# routing from the 2^26-key capture (4096 buckets, as at 2^28), the bucket sort
+# from the 2^27-key capture (65,536-key buckets on clusters of 8, as at 2^28);
+# both kernels stream every key once, so bytes per key carry over to 2^28
+NCU_TRAFFIC = {"route_keys_kernel": ((271.135488e6 + 221.035776e6) / (1 << 26), "20aa65c79b98e17f"),
+               "bucket_keys_kernel": ((537.344768e6 + 488.002560e6) / (1 << 27), "6cd642d19cc0c3ba")}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
-                                       "paper_1408_6729_gb300/csrc/classify.cuh"],
+                                       "paper_1408_6729_gb300/csrc/classify.cuh",
+                                       "paper_1408_6729_gb300/csrc/kernels.cuh"],
                  "bucket_sort_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
                                         "paper_1408_6729_gb300/csrc/segsort.cuh"],
                  "bucket_keys_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",

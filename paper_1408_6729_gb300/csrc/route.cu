@@ -52,21 +52,25 @@ template <typename K> struct RouteFixed {
     LutParams<K> lp;
 };
 
-// Shared memory of the routing kernel.  The splitters' phi live in shared
-// memory when they fit next to the rest, in global memory (L1-cached)
-// otherwise; their tags, read only on ties, stay in global memory.
+// Shared memory of the routing kernel.  The splitters' phi and tags (tags are
+// read on phi ties only, which skewed inputs make common) live in shared
+// memory when they fit next to the rest; the tags, then the phi, stay in
+// global memory (L1-cached) otherwise.
 template <typename K, bool LEARNED = false> struct RouteSmemLayout {
-    size_t mlp, lut, sphi, run, stage_k, stage_v, stage_b, total;
-    bool sphi_in_smem;
+    size_t mlp, lut, sphi, stag, run, stage_k, stage_v, stage_b, total;
+    bool sphi_in_smem, stag_in_smem;
     __host__ __device__ RouteSmemLayout(uint32_t P) {
-        for (int pass = 0; pass < 2; ++pass) {
-            sphi_in_smem = pass == 0;
+        for (int pass = 0; pass < 3; ++pass) {  // splitters' phi and tags, phi only, neither
+            sphi_in_smem = pass < 2;
+            stag_in_smem = pass == 0;
             size_t o = (sizeof(RouteFixed<K>) + 15) & ~size_t(15);
             mlp = o;     o += LEARNED ? sizeof(float) * (kParams + 3) + sizeof(MlpNorm) : 0;
             o = (o + 15) & ~size_t(15);
             lut = o;     o += sizeof(uint16_t) * (kLutCells + 1);
             o = (o + 15) & ~size_t(15);
             sphi = o;    o += sphi_in_smem ? sizeof(K) * (P > 1 ? P - 1 : 1) : 0;
+            o = (o + 15) & ~size_t(15);
+            stag = o;    o += stag_in_smem ? sizeof(uint32_t) * (P > 1 ? P - 1 : 1) : 0;
             o = (o + 15) & ~size_t(15);
             run = o;     o += sizeof(uint32_t) * P;
             o = (o + 15) & ~size_t(15);
@@ -99,7 +103,8 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     uint16_t *lut = reinterpret_cast<uint16_t *>(smem_raw + L.lut);
     K *sphi_s = reinterpret_cast<K *>(smem_raw + L.sphi);
     const K *sphi = L.sphi_in_smem ? sphi_s : a.vphi;
-    const uint32_t *stag = a.vtag;
+    uint32_t *stag_s = reinterpret_cast<uint32_t *>(smem_raw + L.stag);
+    const uint32_t *stag = L.stag_in_smem ? stag_s : a.vtag;
     uint32_t *run = reinterpret_cast<uint32_t *>(smem_raw + L.run);
     K *stage_k = reinterpret_cast<K *>(smem_raw + L.stage_k);
     uint32_t *stage_v = reinterpret_cast<uint32_t *>(smem_raw + L.stage_v);
@@ -112,6 +117,8 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     for (int i = tid; i <= kLutCells; i += TH) lut[i] = a.lut[i];
     if (L.sphi_in_smem)
         for (uint32_t i = tid; i < nsplit; i += TH) sphi_s[i] = a.vphi[i];
+    if (L.stag_in_smem)
+        for (uint32_t i = tid; i < nsplit; i += TH) stag_s[i] = a.vtag[i];
     if constexpr (LEARNED) {
         for (int k = tid; k < kParams; k += TH) mw[k] = a.mlp_params[k];
         if (tid == 0) *mnorm = *a.mlp_norm;

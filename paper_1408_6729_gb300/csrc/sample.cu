@@ -222,17 +222,30 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     const int64_t seg = ((len + W - 1) / W + 31) / 32 * 32;
     const int64_t seg0 = imin64(len, warp * seg), seg1 = imin64(len, seg0 + seg);
     uint32_t *mine = wcnt + warp * NS;
+    // keys of kAhead steps of 32 are loaded before the first is used
+    constexpr int kAhead = 4;
+    uint32_t fa[kAhead];
+    auto load_ahead = [&](int64_t e0) {
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            const int64_t e = e0 + u * 32 + lane;
+            fa[u] = e < seg1 ? (uint32_t)KeyTraits<DT>::phi(keys[lo + e]) : 0u;
+        }
+    };
     // pass 1: distinct values, and their keys per segment
-    for (int64_t e0 = seg0; e0 < seg1; e0 += 32) {
-        const int64_t e = e0 + lane;
-        const bool ok = e < seg1;
-        const uint32_t act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
-            const int h = find(f, true);
-            const uint32_t peers = __match_any_sync(act, f);
-            if (h < 0) overflow = 1;
-            else if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);  // this warp's own counts
+    for (int64_t e0 = seg0; e0 < seg1; e0 += 32 * kAhead) {
+        load_ahead(e0);
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            const bool ok = e0 + u * 32 + lane < seg1;
+            const uint32_t act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const uint32_t f = fa[u];
+                const int h = find(f, true);
+                const uint32_t peers = __match_any_sync(act, f);
+                if (h < 0) overflow = 1;
+                else if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);  // this warp's own counts
+            }
         }
     }
     __syncthreads();
@@ -287,24 +300,28 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     if (tid < nd) start[sid[tid]] = tot_sorted[rank_of[tid]];
     __syncthreads();
     // pass 2: in position order, sorted rank = start + earlier segments + earlier here
-    for (int64_t e0 = seg0; e0 < seg1; e0 += 32) {
-        const int64_t e = e0 + lane;
-        const bool ok = e < seg1;
-        const uint32_t act = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const uint32_t f = (uint32_t)KeyTraits<DT>::phi(keys[lo + e]);
-            const int h = max(0, find(f, false));  // present: every key was counted
-            const uint32_t peers = __match_any_sync(act, f);
-            const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
-            __syncwarp(act);
-            if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
-            if (g1 % xx == 0) {
-                const int64_t j = g1 / xx;
-                sphi[k * s + (j - 1)] = (K)f;
-                stag[k * s + (j - 1)] = (uint32_t)(lo + e);
+    for (int64_t e0 = seg0; e0 < seg1; e0 += 32 * kAhead) {
+        load_ahead(e0);
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            const int64_t e = e0 + u * 32 + lane;
+            const bool ok = e < seg1;
+            const uint32_t act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const uint32_t f = fa[u];
+                const int h = max(0, find(f, false));  // present: every key was counted
+                const uint32_t peers = __match_any_sync(act, f);
+                const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
+                __syncwarp(act);
+                if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
+                if (g1 % xx == 0) {
+                    const int64_t j = g1 / xx;
+                    sphi[k * s + (j - 1)] = (K)f;
+                    stag[k * s + (j - 1)] = (uint32_t)(lo + e);
+                }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
     if (tid == 0) retry[k] = 0;  // done
 }
@@ -352,7 +369,7 @@ __global__ void lsd_hist_kernel(const K *__restrict__ phi, const uint32_t *__res
 
 // table[0] = passes; then (position, src, dst) per pass; table[1+3*NPOS] = final buffer
 template <typename K>
-__global__ void lsd_plan_kernel(const uint32_t *hist, int64_t S, int32_t *table) {
+__global__ void lsd_plan_kernel(const uint32_t *hist, int64_t S, int32_t *table, int phi_only) {
     constexpr int NPOS = 4 + (int)sizeof(K);
     __shared__ int trivial[NPOS];
     if (threadIdx.x < NPOS) trivial[threadIdx.x] = 0;
@@ -362,7 +379,7 @@ __global__ void lsd_plan_kernel(const uint32_t *hist, int64_t S, int32_t *table)
     __syncthreads();
     if (threadIdx.x != 0) return;
     int np = 0, cur = 0;
-    for (int q = 0; q < NPOS; ++q) {
+    for (int q = phi_only ? 4 : 0; q < NPOS; ++q) {
         if (trivial[q]) continue;
         table[1 + 3 * np] = q;
         table[2 + 3 * np] = cur;
@@ -1052,7 +1069,12 @@ template <typename K> static cudaError_t launch_sample_sort_t(const Ctx &c, LsdB
     const int hist_blocks = (int)imin64(1024, (p.sample_size + 1023) / 1024);
     lsd_hist_kernel<K><<<max(hist_blocks, 1), 256, 0, c.stream>>>(b.phi[0], b.tag[0], p.sample_size,
                                                                   c.ly.lsd_hist);
-    lsd_plan_kernel<K><<<1, 256, 0, c.stream>>>(c.ly.lsd_hist, p.sample_size, c.ly.lsd_table);
+    // A regular sample without pads is R runs, each sorted by (phi, tag), in
+    // block order; every tag of a block is below every tag of the next, so a
+    // stable sort by phi alone leaves equal phi in tag order: the tag bytes
+    // need no passes.  (A pad's tag exceeds every key's, so pads break this.)
+    const int phi_only = p.sampling == BSPS_REGULAR && p.n == p.R * p.M;
+    lsd_plan_kernel<K><<<1, 256, 0, c.stream>>>(c.ly.lsd_hist, p.sample_size, c.ly.lsd_table, phi_only);
     if constexpr (sizeof(K) == 4) {
         if (msd_sample_sort(p)) {
             e = p.sample_size > kMsdWideSample ? launch_msd<13>(c, b, hist_blocks) : launch_msd<12>(c, b, hist_blocks);
