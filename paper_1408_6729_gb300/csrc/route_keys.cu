@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
         const int nh = (int)imin64(CH, a.n - e0);
         // ---- classify (Fig. 2 step 9) and rank inside the chunk ----
         uint32_t br[IT];  // bucket << 16 | rank inside the chunk (bucket P: no key)
+        bool agg = true;  // warp-uniform: merge the atomics of lanes sharing lane 0's bucket
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const int q = ((i / V) * T + tid) * V + i % V;
@@ -157,19 +158,26 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
                 kmax = ph > kmax ? ph : kmax;
             }
             // keys of lane 0's bucket are ranked with one atomic (runs of equal
-            // buckets are common in skewed inputs)
-            const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
-            const uint32_t same = __ballot_sync(0xffffffffu, ok && b == b0);
+            // buckets are common in skewed inputs); the warp keeps doing so in
+            // this chunk only if its first two items had such runs
             uint32_t r = 0;
-            if (ok) {
-                if (b != b0) {
-                    r = atomicAdd(&cnt[b], 1u);
-                } else {
-                    const int leader = __ffs(same) - 1;
-                    uint32_t r0 = 0;
-                    if (lane == leader) r0 = atomicAdd(&cnt[b], (uint32_t)__popc(same));
-                    r = __shfl_sync(same, r0, leader) + __popc(same & lanemask_lt());
+            if (i < 2 || agg) {
+                const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+                const uint32_t same = __ballot_sync(0xffffffffu, ok && b == b0);
+                if (i == 0) agg = __popc(same) > 1;
+                if (i == 1) agg |= __popc(same) > 1;
+                if (ok) {
+                    if (b != b0) {
+                        r = atomicAdd(&cnt[b], 1u);
+                    } else {
+                        const int leader = __ffs(same) - 1;
+                        uint32_t r0 = 0;
+                        if (lane == leader) r0 = atomicAdd(&cnt[b], (uint32_t)__popc(same));
+                        r = __shfl_sync(same, r0, leader) + __popc(same & lanemask_lt());
+                    }
                 }
+            } else if (ok) {
+                r = atomicAdd(&cnt[b], 1u);
             }
             br[i] = b << 16 | r;
         }
