@@ -83,7 +83,7 @@ PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "
 # routing from the 2^26-key capture (4096 buckets, as at 2^28), the bucket sort
 # from the 2^27-key capture (65,536-key buckets on clusters of 8, as at 2^28);
 # both kernels stream every key once, so bytes per key carry over to 2^28
-NCU_TRAFFIC = {"route_keys_kernel": ((271.135488e6 + 221.035776e6) / (1 << 26), "20aa65c79b98e17f"),
+NCU_TRAFFIC = {"route_keys_kernel": ((271.315968e6 + 223.367168e6) / (1 << 26), "ac9e5a62a1b9d446"),
                "bucket_keys_kernel": ((537.344768e6 + 488.002560e6) / (1 << 27), "6cd642d19cc0c3ba")}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
