@@ -36,7 +36,7 @@
  * implicit tags (processor id, local array index) of Sec. 5.1.1 in one word.
  * Pads are virtual records that follow every real key.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *  - blocks are contiguous; pads are +infinity records ordered by tag;
  *  - random mode draws positions i.i.d. with replacement:
  *      g_j = floor(h(seed, j) * n / 2^64),  j = 0 .. s*p-2,
