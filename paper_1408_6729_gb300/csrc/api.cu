@@ -361,7 +361,7 @@ const char *bsps_strerror(int status) {
     case BSPS_ERR_BUCKET_OVERFLOW: return "a bucket exceeded its region";
     case BSPS_ERR_CUDA: return "CUDA error";
     case BSPS_ERR_DEVICE_TIMEOUT: return "a bounded device wait expired";
-    case BSPS_ERR_TOO_LARGE: return "problem too large for this build";
+    case BSPS_ERR_TOO_LARGE: return "problem too large for the library's limits (see bsps_get_plan)";
     default: return "unknown status";
     }
 }

@@ -74,7 +74,7 @@ def _run(lib, keys, p, s, runs, mode, seed, vals):
 
 
 def _pins_pass(lib):
-    """True when every pin below accepts this build of the oracle."""
+    """True when every pin below accepts the oracle as it is loaded."""
     # hand-worked Fig. 1 examples
     for path in sorted(glob.glob(os.path.join(GOLDEN, "*.json"))):
         g = json.load(open(path))
