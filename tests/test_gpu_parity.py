@@ -273,3 +273,67 @@ def test_bucket_sort_repeat_rates(dt, span_log2):
     gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 5)
     assert gpu.plan.bucket_cluster == 8
     assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_pairs_one_value_sub_buckets_are_copied(mode):
+    """Payload sort where the two interior buckets lie between equal splitters
+    (one key value holds 90% of the keys): they are copied as they stand, each
+    larger than a cluster's shared memory, while the end buckets mix values and
+    take the cluster or out-of-core sort.  Payloads of equal keys stay in input
+    order (Sec. 5.1.1)."""
+    n, p = 400_000, 4
+    rng = np.random.default_rng(12)
+    u = rng.random(n)
+    keys = np.full(n, 5, np.int32)
+    keys[u < 0.05] = -3
+    keys[u > 0.95] = rng.integers(10, 2**31 - 1, int((u > 0.95).sum()), dtype=np.int64).astype(np.int32)
+    vals = np.arange(n, dtype=np.uint32)
+    if mode == oracle.REGULAR:
+        ref = ref_sort(keys, p, 16, 8, mode, 0, vals)  # blocks of 50,000 keys
+        gpu = run_gpu(keys, p, 16, 8, mode, 0, vals, refine=1)
+    else:
+        ref = ref_sort(keys, p, 0, 0, mode, 4, vals)
+        gpu = run_gpu(keys, p, 0, 0, mode, 4, vals, refine=1)
+    assert_same(gpu, ref)
+
+
+@pytest.mark.parametrize("pad", [0, 5], ids=["no_pads", "pads"])
+def test_regular_keys_with_the_pads_phi(pad):
+    """Regular sampling on keys that include INT32_MAX, whose phi (all ones)
+    is the pads' phi.  With pads (n below R*M) a pad's tag exceeds every key's,
+    so the sample sort must order the tag bytes too; without pads the runs of
+    the sample, in block order, are sorted by phi alone.  Few distinct values:
+    the blocks also take the few-values sampler."""
+    R = p = 16
+    s, m = 64, 4096
+    n = R * m - pad
+    rng = np.random.default_rng(21)
+    keys = rng.choice(np.array([2**31 - 1, 7, -100, 0], np.int32), n, p=[0.4, 0.2, 0.2, 0.2])
+    ref = ref_sort(keys, p, s, R, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, p, s, R, oracle.REGULAR, 0)
+    assert gpu.plan.R * gpu.plan.M - n == pad
+    assert_same(gpu, ref)
+
+
+def test_regular_blocks_at_the_few_values_limit():
+    """Blocks of 257 distinct values (one more than the few-values sampler's
+    table takes) go on to the stable block sort; blocks of 256 stay with the
+    few-values sampler.  Half of every block is one value, so the block sort's
+    probe sends every block to the few-values sampler first."""
+    R = p = 8
+    m, s = 32768, 256
+    rng = np.random.default_rng(31)
+    others = ((np.arange(1, 400, dtype=np.int64) * 16777259) % 2**31 - 2**30).astype(np.int32)
+    blocks = []
+    for k in range(R):
+        d = 257 if k < R // 2 else 256
+        b = np.zeros(m, np.int32)
+        rest = np.concatenate([others[: d - 1], rng.choice(others[: d - 1], m // 2 - (d - 1))])
+        b[m // 2:] = rest
+        blocks.append(rng.permutation(b))
+    keys = np.concatenate(blocks)
+    assert all(len(np.unique(b)) == (257 if k < R // 2 else 256) for k, b in enumerate(blocks))
+    ref = ref_sort(keys, p, s, R, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, p, s, R, oracle.REGULAR, 0)
+    assert_same(gpu, ref)
