@@ -147,7 +147,15 @@ typedef struct {
  * Returns BSPS_ERR_INVALID_ARG when p < 1, n < 0, s < 0, regular mode has
  * R*s not a multiple of p (the splitter stride q = R*s/p of Fig. 1 step 6
  * must be an integer), or refine is not a power of two; BSPS_ERR_TOO_LARGE
- * when n >= 2^30 or the padded key count exceeds 32-bit tags.
+ * when n >= 2^30, s > 2^31 or runs > 2^30, the padded key count n + R*M
+ * reaches 2^32 (32-bit tags), the sample reaches 2^31 records, p or the
+ * sub-bucket count p*refine exceeds 65535 (16-bit ids), in regular mode a
+ * block of ceil(n/R) keys exceeds the block sort's largest cluster (81,920
+ * keys of 4 bytes, 65,536 of 8), the bucket regions exceed 4e9 keys, or the
+ * routing kernel's shared memory (counters per sub-bucket, the radix index,
+ * a staging chunk) exceeds 227 KB for p*refine sub-buckets: with refine = 0
+ * the refinement is lowered first, so this limits p itself to about 12,600
+ * for 4-byte keys without payloads (about 24,700 with payloads).
  */
 int bsps_get_plan(int64_t n, int32_t dtype, const bsps_params *prm, int32_t with_payload,
               bsps_plan *out);
