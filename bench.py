@@ -191,7 +191,11 @@ def barrier(pg):
 
 # ------------------------------------------------------------------ CPU oracle arm
 
-def oracle_rate(wl, budget_s=12.0, seed=1):
+def host_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+def oracle_rate(wl, budget_s=12.0, seed=1, threads=1):
     """Oracle keys/s on a bounded sample of the workload: same generator, p, s,
     runs and mode; n doubles from 2^20 until one sort takes budget_s/4."""
     import oracle
@@ -201,36 +205,74 @@ def oracle_rate(wl, budget_s=12.0, seed=1):
         keys = wl["make"](n, wl["p"], seed)
         vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
         t0 = time.perf_counter()
-        oracle.sort(keys, wl["p"], wl["s"], wl["runs"], wl["sampling"], seed=seed, vals=vals, want_sample=False)
+        oracle.sort(keys, wl["p"], wl["s"], wl["runs"], wl["sampling"], seed=seed, vals=vals, want_sample=False,
+                    threads=threads)
         t = time.perf_counter() - t0
         if t > budget_s / 4 or n >= wl["n"]:
             return n / t, n, wl["s"], wl["runs"], t
         n *= 2
 
 
+def cpu_baselines(wl, p):
+    """The oracle on all host cores (one thread per group of virtual
+    processors, a barrier per superstep) and on one core, and std::sort /
+    std::stable_sort on one core, each on a bounded sample of the workload."""
+    import oracle
+    T = host_threads()
+    rate, ns, s_used, runs_used, t_used = oracle_rate(wl, threads=T)
+    rate1, ns1, _, _, t1 = oracle_rate(wl, budget_s=8.0, threads=1)
+    keys = wl["make"](ns1, wl["p"], 1)
+    std = {}
+    for stable in (False, True):
+        t0 = time.perf_counter()
+        oracle.std_sort(keys, stable=stable)
+        std["std_stable_sort" if stable else "std_sort"] = ns1 / (time.perf_counter() - t0)
+    return {"value": rate, "unit": "keys/s", "cores": T, "kind": "oracle",
+            "sample": f"{ns} keys of the same generator, p={p}, s={s_used}, runs={runs_used or p}, "
+                      f"{t_used:.1f} s on {T} threads",
+            "oracle_1_thread": {"value": rate1, "sample": f"{ns1} keys, {t1:.1f} s"},
+            "std_sort_1_thread": {"value": std["std_sort"], "sample": f"{ns1} keys (keys only)"},
+            "std_stable_sort_1_thread": {"value": std["std_stable_sort"], "sample": f"{ns1} keys (keys only)"},
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu part"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def run_reference(args, wl, name):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
-    rate, n, s, runs, t = oracle_rate(wl, budget_s=min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    T = host_threads()
+    rate, n, s, runs, t = oracle_rate(wl, budget_s=min(12.0, 150.0 / max(1, args.steps + args.warmup)), threads=T)
     times = []
     import oracle
     keys = wl["make"](n, wl["p"], 1)
     vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.sort(keys, wl["p"], s, runs, wl["sampling"], seed=1, vals=vals, want_sample=False)
+        oracle.sort(keys, wl["p"], s, runs, wl["sampling"], seed=1, vals=vals, want_sample=False, threads=T)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     tot = sum(times)
     value = n * len(times) / tot
-    sample = f"{n} keys of the workload's generator, p={wl['p']}, s={s}, runs={runs or wl['p']}, one oracle sort per step"
+    sample = (f"{n} keys of the workload's generator, p={wl['p']}, s={s}, runs={runs or wl['p']}, "
+              f"one oracle sort per step on {T} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if wl.get("dtype") == "f64" else "int32",
             "data": "synthetic", "config": {"workload": name, "n": wl["n"], "p": wl["p"]},
-            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": T, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -315,14 +357,24 @@ def run_gpu(args, wl, name):
     st = bsps.bsps_read_stats(ws)
     if st.status:
         raise RuntimeError(f"device status {bsps.bsps_strerror(st.status)}")
-    # sanity of the last output (not part of the timed region)
-    if f64:
-        ok = bool((kout[1:] >= kout[:-1]).all().item()) and bool(torch.equal(torch.sort(kin).values, kout))
-    else:
-        ok = bool((kout[1:] >= kout[:-1]).all().item()) and int(kout.to(torch.int64).sum().item()) == int(
-            kin.to(torch.int64).sum().item())
-    if not ok:
-        raise RuntimeError("output is not a sorted permutation of the input")
+    # the last output, after the timed region: equal to the input sorted by
+    # torch, and its bucket sizes equal to the oracle's (same keys and seed)
+    if not torch.equal(torch.sort(kin).values, kout):
+        raise RuntimeError("output differs from the sorted input")
+    verified = None
+    if not args.no_verify and rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.sort(keys_h, p, wl["s"], wl["runs"], wl["sampling"], seed=prm.seed, want_sample=False,
+                          vals=np.arange(n, dtype=np.uint32) if wl["pairs"] else None, threads=host_threads())
+        if not np.array_equal(sizes.cpu().numpy(), ref.bucket_sizes):
+            raise RuntimeError("bucket sizes differ from the oracle's")
+        if wl["pairs"] and not np.array_equal(vout.cpu().numpy().view(np.uint32), ref.vals):
+            raise RuntimeError("payloads differ from the oracle's")
+        verified = {"sorted_equals_torch_sort": True, "bucket_sizes_equal_oracle": True,
+                    "payloads_equal_oracle": True if wl["pairs"] else None,
+                    "oracle_s": round(time.perf_counter() - t0, 1)}
+        del ref
     compare = None
     if wl.get("compare") == "tree":
         compare = compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st, stream, elapsed_ms)
@@ -336,7 +388,7 @@ def run_gpu(args, wl, name):
     if rank != 0:
         return
     return report(args, wl, name, world, n, p, plan, st, per_step_of(phase_ms, args), elapsed_ms, e2e_ms,
-                  e2e_steps, total_launches, clk, compare)
+                  e2e_steps, total_launches, clk, compare, verified)
 
 
 def compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st_learned, stream, learned_ms):
@@ -426,7 +478,7 @@ def run_e2e(args, stream, kin, kout, keys_h, step, pg, n):
 
 
 def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, e2e_steps, total_launches, clk,
-           compare=None):
+           compare=None, verified=None):
     pk, pk_kind = peaks()
     key_bytes = 8 if wl.get("dtype") == "f64" else 4
     kb = key_bytes + (4 if wl["pairs"] else 0)
@@ -444,10 +496,7 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     b_alg = 4 * kb + plan.sample_size * (key_bytes + 2 * rec) / n + (kb if wl["sampling"] == 0 else 0)
     cpu = None
     if world == 1 and not args.no_baseline and wl.get("dtype") != "f64":
-        rate, ns, s_used, runs_used, t_used = oracle_rate(wl)
-        cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
-               "sample": f"{ns} keys of the same generator, p={p}, s={s_used}, "
-                         f"runs={runs_used or p}, {t_used:.1f} s single-threaded"}
+        cpu = cpu_baselines(wl, p)
     line = {
         "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -478,6 +527,8 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     }
     if compare is not None:
         line["learned_vs_tree"] = compare
+    if verified is not None:
+        line["verified"] = verified
     print(json.dumps(line), flush=True)
 
 
@@ -656,6 +707,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg (profiling runs)")
     ap.add_argument("--refine", type=int, default=0, help="sub-buckets per bucket (0: the library's choice)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-verify", action="store_true",
+                    help="skip the oracle comparison of the last output (profiling runs)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

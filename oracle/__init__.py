@@ -20,6 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bsp_oracle.c")
 _LIB = os.path.join(_HERE, "libbsp_oracle.so")
+_STD_SRC = os.path.join(_HERE, "std_sorts.cpp")
+_STD_LIB = os.path.join(_HERE, "libstd_sorts.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -32,7 +34,7 @@ DTYPE_CODE = {np.dtype(np.uint32): U32, np.dtype(np.int32): I32,
 
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("runs", ctypes.c_int32), ("s", ctypes.c_int64),
-                ("sampling", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sampling", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -51,9 +53,13 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
                                    "-o", tmp, _SRC])
             os.replace(tmp, _LIB)
+        if force or not os.path.exists(_STD_LIB) or os.path.getmtime(_STD_LIB) < os.path.getmtime(_STD_SRC):
+            tmp = _STD_LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _STD_SRC])
+            os.replace(tmp, _STD_LIB)
     return _LIB
 
 
@@ -75,12 +81,32 @@ def _load():
     return _lib
 
 
+_std = None
+
+
+def std_sort(keys: np.ndarray, stable: bool = False) -> np.ndarray:
+    """The keys sorted by std::sort (or std::stable_sort), single-threaded: a
+    CPU baseline timed beside the oracle, not part of it."""
+    global _std
+    if _std is None:
+        build()
+        lib = ctypes.CDLL(_STD_LIB)
+        lib.baseline_std_sort.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+        lib.baseline_std_sort.restype = ctypes.c_int
+        _std = lib
+    out = np.array(keys, copy=True, order="C")
+    rc = _std.baseline_std_sort(DTYPE_CODE[out.dtype], out.ctypes.data, out.shape[0], int(stable))
+    if rc:
+        raise ValueError("std_sort failed")
+    return out
+
+
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def make_params(p, s=0, runs=0, sampling=REGULAR, seed=0) -> Params:
-    return Params(p=int(p), runs=int(runs), s=int(s), sampling=int(sampling), reserved=0,
+def make_params(p, s=0, runs=0, sampling=REGULAR, seed=0, threads=0) -> Params:
+    return Params(p=int(p), runs=int(runs), s=int(s), sampling=int(sampling), threads=int(threads),
                   seed=int(seed) & (2**64 - 1))
 
 
@@ -115,8 +141,11 @@ class Result:
 
 def sort(keys: np.ndarray, p: int, s: int = 0, runs: int = 0, sampling: int = REGULAR,
          seed: int = 0, vals: np.ndarray | None = None, want_sample: bool = True,
-         want_bucket_of: bool = False) -> Result:
-    """Run the BSP simulation; raises ValueError on invalid parameters."""
+         want_bucket_of: bool = False, threads: int = 0) -> Result:
+    """Run the BSP simulation; raises ValueError on invalid parameters.
+
+    threads > 1 runs the virtual processors of each superstep on that many host
+    threads (the result is the same)."""
     keys = np.ascontiguousarray(keys)
     code = DTYPE_CODE[keys.dtype]
     n = keys.shape[0]
@@ -133,7 +162,7 @@ def sort(keys: np.ndarray, p: int, s: int = 0, runs: int = 0, sampling: int = RE
     sample = np.zeros(pl.sample_size, RECORD_DTYPE) if (want_sample and n > 0) else None
     spl = np.zeros(max(pl.p - 1, 0), RECORD_DTYPE)
     bof = np.full(n, -1, np.int32) if want_bucket_of else None
-    prm = make_params(p, s, runs, sampling, seed)
+    prm = make_params(p, s, runs, sampling, seed, threads)
     rc = _load().oracle_sort(code, _ptr(keys), _ptr(vals), n, ctypes.byref(prm), _ptr(keys_out),
                              _ptr(vals_out), _ptr(sizes), _ptr(pads), _ptr(sample), _ptr(spl),
                              _ptr(bof))

@@ -28,6 +28,11 @@
  *   SS7 prefix      per-bucket counts and receive offsets (Fig. 1 step 9)
  *   SS8 route       order-preserving all-to-all (Fig. 1 steps 10-11)
  *   SS9 merge       stable multi-way merge of each bucket (Fig. 1 step 12)
+ * Each superstep is a function of one processor id; all processors run it,
+ * one after the other or on several host threads (params.threads), and the
+ * next superstep starts only when every processor has finished (the barrier
+ * of the BSP model).  Processors of one superstep write disjoint memory, so
+ * the result does not depend on the number of threads.
  *
  * The total order (Sec. 5.1.1): records compare by (pad, phi(key), tag).
  * phi maps a key's bit pattern to an unsigned integer whose unsigned order is
@@ -45,6 +50,7 @@
  *  - splitter i is the sorted-sample record of 1-indexed rank i*q
  *    (q = R*s/p regular, q = s random), and belongs to the upper bucket.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -69,7 +75,7 @@ typedef struct {
     int32_t runs;     /* R virtual processors; 0 -> p */
     int64_t s;        /* oversampling factor; 0 -> paper default */
     int32_t sampling; /* OR_REGULAR or OR_RANDOM */
-    int32_t reserved;
+    int32_t threads;  /* host threads running the processors; 0 -> 1 */
     uint64_t seed;    /* random-mode sample seed */
 } oracle_params;
 
@@ -236,6 +242,232 @@ static void to_record(const elem *e, oracle_record *r) {
     r->phi = e->phi; r->tag = e->tag; r->pad = e->pad; r->reserved = 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* The simulated BSP machine.  A superstep runs the same local computation
+ * on every virtual processor, then all processors meet at a barrier before
+ * the next superstep reads what the others produced (the BSP model, Sec. 2).
+ * The local computations of one superstep touch disjoint data, so they may
+ * run on several host threads; the join of those threads is the barrier.
+ * With one thread the processors simply run one after the other.         */
+
+typedef struct {
+    int dtype;
+    const void *keys;
+    const uint32_t *vals;
+    uint64_t seed;
+    oracle_plan pl;
+    int regular;
+    elem **local;         /* local[k]: the records held by processor k */
+    int64_t *len;         /* records held (keys and pads) */
+    int64_t *nreal;       /* real keys held */
+    elem *Y;              /* the sample, gathered at processor 0 */
+    elem *Spl;            /* the p-1 splitters */
+    elem **Sk;            /* Sk[k]: processor k's copy of the splitters */
+    int64_t *c;           /* c[k*(p+1)+i]: first position of segment i in block k */
+    int64_t *bucket_len;  /* records received by processor i (keys and pads) */
+    int64_t *bucket_real; /* real keys received by processor i */
+    int64_t *out_off;     /* output position of processor i's first key */
+    int64_t *recv_off;    /* recv_off[k*p+i]: where X^k_i lands in Z^i */
+    elem **Z;             /* Z[i]: the segments received by processor i */
+    void *keys_out;
+    uint32_t *vals_out;
+    int64_t *pad_sizes;
+    int32_t *bucket_of;
+    int failed;           /* some processor could not allocate its memory */
+} machine;
+
+typedef void (*local_step)(machine *S, int64_t k);
+
+typedef struct {
+    machine *S;
+    local_step fn;
+    int64_t count;
+    int threads, t;
+} worker;
+
+static void *run_worker(void *arg) {
+    worker *w = (worker *)arg;
+    for (int64_t k = w->t; k < w->count; k += w->threads) w->fn(w->S, k);
+    return NULL;
+}
+
+/* run fn(S, k) for k = 0 .. count-1, then the barrier */
+static void superstep(machine *S, int threads, int64_t count, local_step fn) {
+    if (threads > count) threads = (int)count;
+    if (threads <= 1) {
+        for (int64_t k = 0; k < count; ++k) fn(S, k);
+        return;
+    }
+    pthread_t th[256];
+    worker w[256];
+    if (threads > 256) threads = 256;
+    int started = 1;
+    for (int t = 0; t < threads; ++t) w[t] = (worker){S, fn, count, threads, t};
+    for (int t = 1; t < threads; ++t, ++started)
+        if (pthread_create(&th[t], NULL, run_worker, &w[t])) break;
+    /* a worker that could not be started: the calling thread takes its share */
+    for (int t = started; t < threads; ++t) {
+        w[t].threads = threads;
+        run_worker(&w[t]);
+    }
+    run_worker(&w[0]);
+    for (int t = 1; t < started; ++t) pthread_join(th[t], NULL);
+}
+
+static void fail(machine *S) { __atomic_store_n(&S->failed, 1, __ATOMIC_RELAXED); }
+
+/* ---- SS0: processor k receives the contiguous block [k*m, (k+1)*m) and pads
+ *      it to M records in regular mode (Lemma 5.1 proof) ---- */
+static void ss0_distribute(machine *S, int64_t k) {
+    const oracle_plan pl = S->pl;
+    const int64_t m = pl.m, M = pl.M, n = pl.n;
+    int64_t lo = k * m, hi = lo + m < n ? lo + m : n;
+    S->nreal[k] = hi > lo ? hi - lo : 0;
+    S->len[k] = S->regular ? M : S->nreal[k];
+    elem *blk = malloc(sizeof(elem) * (size_t)(S->len[k] ? S->len[k] : 1));
+    S->local[k] = blk;
+    if (!blk) { fail(S); return; }
+    for (int64_t j = 0; j < S->len[k]; ++j) {
+        elem *e = &blk[j];
+        e->tag = (uint64_t)(k * M + j);
+        if (j < S->nreal[k]) {
+            e->phi = phi_of(S->dtype, key_bits(S->dtype, S->keys, lo + j));
+            e->val = S->vals ? S->vals[lo + j] : 0;
+            e->pad = 0;
+        } else {
+            e->phi = ~0ull;
+            e->val = 0;
+            e->pad = 1;
+        }
+    }
+}
+
+/* ---- SS1: local sort on processor k (Fig. 1/3 step 3) ---- */
+static void ss1_local_sort(machine *S, int64_t k) {
+    if (S->local[k]) qsort(S->local[k], (size_t)S->len[k], sizeof(elem), elem_cmp);
+}
+
+/* ---- SS2 (regular): processor k's sample, the last key of each of its s
+ *      segments of x keys (Fig. 1 step 4) ---- */
+static void ss2_regular_sample(machine *S, int64_t k) {
+    elem **local = S->local, *Y = S->Y;
+    const oracle_plan pl = S->pl;
+    for (int64_t j = 1; j <= pl.s; ++j) Y[k * pl.s + (j - 1)] = local[k][j * pl.x - 1];
+}
+
+/* ---- SS5: processor k receives its copy of the splitters (Fig. 1 step 7) ---- */
+static void ss5_broadcast(machine *S, int64_t k) {
+    const int64_t p = S->pl.p;
+    S->Sk[k] = malloc(sizeof(elem) * (size_t)(p > 1 ? p - 1 : 1));
+    if (!S->Sk[k]) { fail(S); return; }
+    memcpy(S->Sk[k], S->Spl, sizeof(elem) * (size_t)(p - 1));
+}
+
+/* ---- SS6: processor k partitions its sorted block by binary search of each
+ *      splitter; segment i = [c[i], c[i+1]) (Sec. 5.1 step 9) ---- */
+static void ss6_partition(machine *S, int64_t k) {
+    elem **local = S->local, **Sk = S->Sk;
+    const int64_t p = S->pl.p;
+    int64_t *ck = S->c + k * (p + 1);
+    ck[0] = 0;
+    ck[p] = S->len[k];
+    for (int64_t i = 1; i < p; ++i) {
+        /* first local position whose record is not smaller than S_i */
+        int64_t lo = 0, hi = S->len[k];
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (elem_less(&local[k][mid], &Sk[k][i - 1])) lo = mid + 1;
+            else hi = mid;
+        }
+        ck[i] = lo;
+    }
+}
+
+/* ---- SS7: counts of bucket i and the receive offsets of its segments
+ *      (Fig. 1 step 9) ---- */
+static void ss7_prefix(machine *S, int64_t i) {
+    elem **local = S->local;
+    const int64_t p = S->pl.p, R = S->pl.R;
+    int64_t *pad_sizes = S->pad_sizes;
+    int64_t acc = 0, real = 0;
+    for (int64_t k = 0; k < R; ++k) {
+        const int64_t *ck = S->c + k * (p + 1);
+        S->recv_off[k * p + i] = acc;
+        acc += ck[i + 1] - ck[i];
+        for (int64_t t = ck[i]; t < ck[i + 1]; ++t) {
+            if (local[k][t].pad) { if (pad_sizes) pad_sizes[i]++; }
+            else real++;
+        }
+    }
+    S->bucket_len[i] = acc;
+    S->bucket_real[i] = real;
+}
+
+/* ---- SS8: processor i receives X^k_i from every k, in processor order
+ *      (Fig. 1 step 11) ---- */
+static void ss8_route(machine *S, int64_t i) {
+    elem **local = S->local;
+    const int64_t p = S->pl.p, R = S->pl.R;
+    S->Z[i] = malloc(sizeof(elem) * (size_t)(S->bucket_len[i] ? S->bucket_len[i] : 1));
+    if (!S->Z[i]) { fail(S); return; }
+    for (int64_t k = 0; k < R; ++k) {
+        const int64_t *ck = S->c + k * (p + 1);
+        memcpy(S->Z[i] + S->recv_off[k * p + i], local[k] + ck[i],
+               sizeof(elem) * (size_t)(ck[i + 1] - ck[i]));
+    }
+}
+
+/* ---- SS9: processor i merges its received sorted segments stably (Fig. 1
+ *      step 12; ties by source processor, Sec. 5.1.1) and emits its keys ---- */
+static void ss9_merge(machine *S, int64_t i) {
+    const int64_t p = S->pl.p, R = S->pl.R, m = S->pl.m, M = S->pl.M;
+    const int64_t *c = S->c;
+    head *h = malloc(sizeof(head) * (size_t)(R ? R : 1));
+    if (!h) { fail(S); return; }
+    int64_t out = S->out_off[i];
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < R; ++k) {
+        int64_t seg_len = c[k * (p + 1) + i + 1] - c[k * (p + 1) + i];
+        if (seg_len > 0) {
+            h[cnt].seg = S->Z[i] + S->recv_off[k * p + i];
+            h[cnt].len = seg_len;
+            h[cnt].pos = 0;
+            ++cnt;
+        }
+    }
+    for (int64_t t = cnt / 2 - 1; t >= 0; --t) heap_down(h, cnt, t);
+    while (cnt > 0) {
+        const elem *e = &h[0].seg[h[0].pos];
+        if (!e->pad) { /* pads are dropped from the output */
+            put_key(S->dtype, S->keys_out, out, key_of_phi(S->dtype, e->phi));
+            if (S->vals_out) S->vals_out[out] = e->val;
+            if (S->bucket_of) {
+                int64_t k = (int64_t)(e->tag / (uint64_t)M), j = (int64_t)(e->tag % (uint64_t)M);
+                S->bucket_of[k * m + j] = (int32_t)i;
+            }
+            ++out;
+        }
+        if (++h[0].pos == h[0].len) h[0] = h[--cnt];
+        if (cnt > 0) heap_down(h, cnt, 0);
+    }
+    free(h);
+}
+
+static void free_block(machine *S, int64_t k) {
+    free(S->local[k]);
+    S->local[k] = NULL;
+}
+
+static void release(machine *S) {
+    const int64_t R = S->pl.R, p = S->pl.p;
+    if (S->local) for (int64_t k = 0; k < R; ++k) free(S->local[k]);
+    if (S->Sk) for (int64_t k = 0; k < R; ++k) free(S->Sk[k]);
+    if (S->Z) for (int64_t i = 0; i < p; ++i) free(S->Z[i]);
+    free(S->local); free(S->len); free(S->nreal); free(S->Y); free(S->Spl); free(S->Sk);
+    free(S->c); free(S->bucket_len); free(S->bucket_real); free(S->out_off); free(S->recv_off);
+    free(S->Z);
+}
+
 /*
  * oracle_sort: sort n keys (and optional 32-bit payloads) by the BSP
  * simulation above.  Outputs (each optional unless noted):
@@ -246,6 +478,8 @@ static void to_record(const elem *e, oracle_record *r) {
  *   sample        plan.sample_size sorted sample records
  *   splitters     p-1 splitter records
  *   bucket_of     n bucket ids, indexed by the input position
+ * prm->threads host threads run the processors of each superstep (0 or 1:
+ * one after the other); the result does not depend on it.
  */
 int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
                 const oracle_params *prm, void *keys_out, uint32_t *vals_out,
@@ -255,52 +489,51 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     oracle_plan pl;
     int rc = oracle_plan_of(n, prm, &pl);
     if (rc) return rc;
-    const int64_t p = pl.p, R = pl.R, m = pl.m, M = pl.M, S = pl.sample_size;
-    const int regular = pl.sampling == OR_REGULAR;
+    const int64_t p = pl.p, R = pl.R, m = pl.m, M = pl.M, S_ = pl.sample_size;
+    const int T = prm->threads > 1 ? prm->threads : 1;
     if (bucket_sizes) memset(bucket_sizes, 0, sizeof(int64_t) * p);
     if (pad_sizes) memset(pad_sizes, 0, sizeof(int64_t) * p);
     if (n == 0) return OR_OK;
 
-    /* ---- SS0: distribute contiguous blocks; pad them (Lemma 5.1 proof) ---- */
-    elem **local = calloc((size_t)R, sizeof(elem *));
-    int64_t *len = calloc((size_t)R, sizeof(int64_t));     /* records held */
-    int64_t *nreal = calloc((size_t)R, sizeof(int64_t));   /* real keys held */
-    if (!local || !len || !nreal) return OR_ENOMEM;
-    for (int64_t k = 0; k < R; ++k) {
-        int64_t lo = k * m, hi = lo + m < n ? lo + m : n;
-        nreal[k] = hi > lo ? hi - lo : 0;
-        len[k] = regular ? M : nreal[k];
-        local[k] = malloc(sizeof(elem) * (size_t)(len[k] ? len[k] : 1));
-        if (!local[k]) return OR_ENOMEM;
-        for (int64_t j = 0; j < len[k]; ++j) {
-            elem *e = &local[k][j];
-            e->tag = (uint64_t)(k * M + j);
-            if (j < nreal[k]) {
-                e->phi = phi_of(dtype, key_bits(dtype, keys, lo + j));
-                e->val = vals ? vals[lo + j] : 0;
-                e->pad = 0;
-            } else {
-                e->phi = ~0ull;
-                e->val = 0;
-                e->pad = 1;
-            }
-        }
+    machine mc;
+    memset(&mc, 0, sizeof(mc));
+    machine *S = &mc;
+    S->dtype = dtype; S->keys = keys; S->vals = vals; S->seed = prm->seed; S->pl = pl;
+    S->regular = pl.sampling == OR_REGULAR;
+    S->keys_out = keys_out; S->vals_out = vals_out; S->pad_sizes = pad_sizes; S->bucket_of = bucket_of;
+    S->local = calloc((size_t)R, sizeof(elem *));
+    S->len = calloc((size_t)R, sizeof(int64_t));
+    S->nreal = calloc((size_t)R, sizeof(int64_t));
+    S->Y = malloc(sizeof(elem) * (size_t)(S_ ? S_ : 1));
+    S->Spl = malloc(sizeof(elem) * (size_t)(p > 1 ? p - 1 : 1));
+    S->Sk = calloc((size_t)R, sizeof(elem *));
+    S->c = malloc(sizeof(int64_t) * (size_t)R * (size_t)(p + 1));
+    S->bucket_len = calloc((size_t)p, sizeof(int64_t));
+    S->bucket_real = calloc((size_t)p, sizeof(int64_t));
+    S->out_off = calloc((size_t)p, sizeof(int64_t));
+    S->recv_off = malloc(sizeof(int64_t) * (size_t)R * (size_t)p);
+    S->Z = calloc((size_t)p, sizeof(elem *));
+    if (!S->local || !S->len || !S->nreal || !S->Y || !S->Spl || !S->Sk || !S->c || !S->bucket_len ||
+        !S->bucket_real || !S->out_off || !S->recv_off || !S->Z) {
+        release(S);
+        return OR_ENOMEM;
     }
+    elem *Y = S->Y, *Spl = S->Spl;
+
+    /* ---- SS0: distribute contiguous blocks; pad them (Lemma 5.1 proof) ---- */
+    superstep(S, T, R, ss0_distribute);
+    if (S->failed) { release(S); return OR_ENOMEM; }
 
     /* ---- SS1: local sort on every processor (Fig. 1/3 step 3) ---- */
-    for (int64_t k = 0; k < R; ++k) qsort(local[k], (size_t)len[k], sizeof(elem), elem_cmp);
+    superstep(S, T, R, ss1_local_sort);
 
     /* ---- SS2: sample (Fig. 1 step 4 / Fig. 3 step 4) ---- */
-    elem *Y = malloc(sizeof(elem) * (size_t)(S ? S : 1));
-    if (!Y) return OR_ENOMEM;
-    if (regular) {
-        /* processor k: the last key of each of its s segments of x keys */
-        for (int64_t k = 0; k < R; ++k)
-            for (int64_t j = 1; j <= pl.s; ++j) Y[k * pl.s + (j - 1)] = local[k][j * pl.x - 1];
+    if (S->regular) {
+        superstep(S, T, R, ss2_regular_sample);
     } else {
         /* s*p-1 keys chosen uniformly at random; the processor owning
          * input position g contributes the record of that key */
-        for (int64_t j = 0; j < S; ++j) {
+        for (int64_t j = 0; j < S_; ++j) {
             int64_t g = oracle_position(prm->seed, (uint64_t)j, n);
             int64_t k = g / m, jj = g - k * m;
             elem e;
@@ -313,114 +546,42 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     }
 
     /* ---- SS3: sample sort at one processor (Fig. 1 step 5) ---- */
-    qsort(Y, (size_t)S, sizeof(elem), elem_cmp);
+    qsort(Y, (size_t)S_, sizeof(elem), elem_cmp);
     if (sample)
-        for (int64_t t = 0; t < S; ++t) to_record(&Y[t], &sample[t]);
+        for (int64_t t = 0; t < S_; ++t) to_record(&Y[t], &sample[t]);
 
     /* ---- SS4: p-1 evenly spaced splitters, 1-indexed rank i*q (Fig. 1 step 6) ---- */
-    elem *Spl = malloc(sizeof(elem) * (size_t)(p > 1 ? p - 1 : 1));
-    if (!Spl) return OR_ENOMEM;
     for (int64_t i = 1; i < p; ++i) Spl[i - 1] = Y[i * pl.q - 1];
     if (splitters)
         for (int64_t i = 1; i < p; ++i) to_record(&Spl[i - 1], &splitters[i - 1]);
 
     /* ---- SS5: broadcast (Fig. 1 step 7): every processor gets a copy ---- */
-    elem **Sk = calloc((size_t)R, sizeof(elem *));
-    if (!Sk) return OR_ENOMEM;
-    for (int64_t k = 0; k < R; ++k) {
-        Sk[k] = malloc(sizeof(elem) * (size_t)(p > 1 ? p - 1 : 1));
-        if (!Sk[k]) return OR_ENOMEM;
-        memcpy(Sk[k], Spl, sizeof(elem) * (size_t)(p - 1));
-    }
+    superstep(S, T, R, ss5_broadcast);
+    if (S->failed) { release(S); return OR_ENOMEM; }
 
     /* ---- SS6: partition by binary search of each splitter into the sorted
-     *      local keys; segment i = [c[i], c[i+1]) (Sec. 5.1 step 9) ---- */
-    int64_t *c = malloc(sizeof(int64_t) * (size_t)R * (size_t)(p + 1));
-    if (!c) return OR_ENOMEM;
-    for (int64_t k = 0; k < R; ++k) {
-        int64_t *ck = c + k * (p + 1);
-        ck[0] = 0;
-        ck[p] = len[k];
-        for (int64_t i = 1; i < p; ++i) {
-            /* first local position whose record is not smaller than S_i */
-            int64_t lo = 0, hi = len[k];
-            while (lo < hi) {
-                int64_t mid = lo + (hi - lo) / 2;
-                if (elem_less(&local[k][mid], &Sk[k][i - 1])) lo = mid + 1;
-                else hi = mid;
-            }
-            ck[i] = lo;
-        }
-    }
+     *      local keys (Sec. 5.1 step 9) ---- */
+    superstep(S, T, R, ss6_partition);
 
     /* ---- SS7: per-bucket counts and prefix sums (Fig. 1 step 9) ---- */
-    int64_t *bucket_len = calloc((size_t)p, sizeof(int64_t));
-    int64_t *recv_off = malloc(sizeof(int64_t) * (size_t)R * (size_t)p);
-    if (!bucket_len || !recv_off) return OR_ENOMEM;
+    superstep(S, T, p, ss7_prefix);
+    int64_t acc = 0;
     for (int64_t i = 0; i < p; ++i) {
-        int64_t acc = 0;
-        for (int64_t k = 0; k < R; ++k) {
-            const int64_t *ck = c + k * (p + 1);
-            recv_off[k * p + i] = acc;
-            acc += ck[i + 1] - ck[i];
-            for (int64_t t = ck[i]; t < ck[i + 1]; ++t) {
-                if (local[k][t].pad) { if (pad_sizes) pad_sizes[i]++; }
-                else if (bucket_sizes) bucket_sizes[i]++;
-            }
-        }
-        bucket_len[i] = acc;
+        S->out_off[i] = acc;
+        acc += S->bucket_real[i];
+        if (bucket_sizes) bucket_sizes[i] = S->bucket_real[i];
     }
 
     /* ---- SS8: route X^k_i to Z^i_k, sources in processor order (Fig. 1 step 11) ---- */
-    elem **Z = calloc((size_t)p, sizeof(elem *));
-    if (!Z) return OR_ENOMEM;
-    for (int64_t i = 0; i < p; ++i) {
-        Z[i] = malloc(sizeof(elem) * (size_t)(bucket_len[i] ? bucket_len[i] : 1));
-        if (!Z[i]) return OR_ENOMEM;
-    }
-    for (int64_t k = 0; k < R; ++k) {
-        const int64_t *ck = c + k * (p + 1);
-        for (int64_t i = 0; i < p; ++i)
-            memcpy(Z[i] + recv_off[k * p + i], local[k] + ck[i],
-                   sizeof(elem) * (size_t)(ck[i + 1] - ck[i]));
-    }
+    superstep(S, T, p, ss8_route);
+    if (S->failed) { release(S); return OR_ENOMEM; }
+    superstep(S, T, R, free_block);  /* the routed records now live in Z */
 
     /* ---- SS9: stable multi-way merge of the received sorted segments
      *      (Fig. 1 step 12; ties by source processor, Sec. 5.1.1) ---- */
-    head *h = malloc(sizeof(head) * (size_t)R);
-    if (!h) return OR_ENOMEM;
-    int64_t out = 0;
-    for (int64_t i = 0; i < p; ++i) {
-        int64_t cnt = 0;
-        for (int64_t k = 0; k < R; ++k) {
-            int64_t seg_len = c[k * (p + 1) + i + 1] - c[k * (p + 1) + i];
-            if (seg_len > 0) {
-                h[cnt].seg = Z[i] + recv_off[k * p + i];
-                h[cnt].len = seg_len;
-                h[cnt].pos = 0;
-                ++cnt;
-            }
-        }
-        for (int64_t t = cnt / 2 - 1; t >= 0; --t) heap_down(h, cnt, t);
-        while (cnt > 0) {
-            const elem *e = &h[0].seg[h[0].pos];
-            if (!e->pad) { /* pads are dropped from the output */
-                put_key(dtype, keys_out, out, key_of_phi(dtype, e->phi));
-                if (vals_out) vals_out[out] = e->val;
-                if (bucket_of) {
-                    int64_t k = (int64_t)(e->tag / (uint64_t)M), j = (int64_t)(e->tag % (uint64_t)M);
-                    bucket_of[k * m + j] = (int32_t)i;
-                }
-                ++out;
-            }
-            if (++h[0].pos == h[0].len) h[0] = h[--cnt];
-            if (cnt > 0) heap_down(h, cnt, 0);
-        }
-    }
-
-    for (int64_t k = 0; k < R; ++k) { free(local[k]); free(Sk[k]); }
-    for (int64_t i = 0; i < p; ++i) free(Z[i]);
-    free(local); free(len); free(nreal); free(Y); free(Spl); free(Sk); free(c);
-    free(bucket_len); free(recv_off); free(Z); free(h);
-    return out == n ? OR_OK : OR_EINVAL;
+    superstep(S, T, p, ss9_merge);
+    const int failed = S->failed;
+    release(S);
+    if (failed) return OR_ENOMEM;
+    return acc == n ? OR_OK : OR_EINVAL;
 }

@@ -1,6 +1,7 @@
 // sample.cu -- oversampling, sample sort, splitter selection (Fig. 1 steps
 // 3-7, Fig. 3 steps 3-9) and the optional diagnostics.
 #include "classify.cuh"
+#include "mlp.cuh"
 #include "segsort.cuh"
 #include "segsort_keys.cuh"
 
@@ -916,15 +917,30 @@ __global__ void splitter_records_kernel(const K *vphi, const uint32_t *vtag, int
     if (i < p) out[i - 1] = to_record(vphi[i * B - 1], vtag[i * B - 1], n, m, M, regular);
 }
 
-template <int DT>
-__global__ void bucket_of_kernel(const typename KeyTraits<DT>::T *keys, int64_t n, int64_t B,
+// Per-key buckets of the keys (diagnostics).  With the learned classifier
+// every key goes through the same classify_learned (prediction + correction)
+// the routing kernel uses, so its result can be compared key by key.
+template <int DT, bool LEARNED>
+__global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits<DT>::T *keys, int64_t n, int64_t B,
                                  const typename KeyTraits<DT>::T *vphi, const uint32_t *vtag,
                                  const uint16_t *lut,
-                                 const LutParams<typename KeyTraits<DT>::T> *lutp, int32_t *out) {
+                                 const LutParams<typename KeyTraits<DT>::T> *lutp, const float *mlp_params,
+                                 const MlpNorm *mlp_norm, int64_t P, int32_t *out) {
+    __shared__ __align__(16) float w[LEARNED ? kParams + 3 : 1];
+    if constexpr (LEARNED) {
+        for (int q = threadIdx.x; q < kParams; q += blockDim.x) w[q] = mlp_params[q];
+        __syncthreads();
+    }
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
-    const LutParams<typename KeyTraits<DT>::T> lp = *lutp;
-    const uint32_t v = classify_key(KeyTraits<DT>::phi(keys[g]), (uint32_t)g, lp, lut, vphi, vtag);
+    uint32_t v;
+    if constexpr (LEARNED) {
+        uint32_t steps;
+        v = classify_learned<DT>(keys[g], (uint32_t)g, w, *mlp_norm, (uint32_t)P, vphi, vtag, steps);
+    } else {
+        const LutParams<typename KeyTraits<DT>::T> lp = *lutp;
+        v = classify_key(KeyTraits<DT>::phi(keys[g]), (uint32_t)g, lp, lut, vphi, vtag);
+    }
     out[g] = (int32_t)(v / B);
 }
 
@@ -1142,10 +1158,12 @@ template <int DT> static cudaError_t launch_debug_t(const Ctx &c) {
     if (c.dbg.splitters && p.p > 1)
         splitter_records_kernel<K><<<(unsigned)((p.p + 255) / 256), 256, 0, c.stream>>>(
             (const K *)c.ly.vphi, c.ly.vtag, p.p, p.B, p.n, p.m, p.M, regular, c.dbg.splitters);
-    if (c.dbg.bucket_of && p.n > 0)
-        bucket_of_kernel<DT><<<(unsigned)((p.n + 255) / 256), 256, 0, c.stream>>>(
+    if (c.dbg.bucket_of && p.n > 0) {
+        auto kern = p.classify == BSPS_LEARNED ? bucket_of_kernel<DT, true> : bucket_of_kernel<DT, false>;
+        kern<<<(unsigned)((p.n + 255) / 256), 256, 0, c.stream>>>(
             (const K *)c.keys_in, p.n, p.B, (const K *)c.ly.vphi, c.ly.vtag, c.ly.lut,
-            (const LutParams<K> *)c.ly.lutp, c.dbg.bucket_of);
+            (const LutParams<K> *)c.ly.lutp, c.ly.mlp_params, c.ly.mlp_norm, p.P, c.dbg.bucket_of);
+    }
     if (c.dbg.pad_sizes) {
         cudaError_t e = cudaMemsetAsync(c.dbg.pad_sizes, 0, sizeof(int64_t) * p.p, c.stream);
         if (e != cudaSuccess) return e;

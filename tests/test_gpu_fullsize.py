@@ -1,0 +1,88 @@
+"""Every quoted 2^28 configuration against the oracle at its stated size.
+
+The GPU result of each configuration the measurements are quoted on is
+compared element by element with the oracle (Fig. 1 / Fig. 3 as an explicit
+BSP simulation, run on all host cores, one thread per group of virtual
+processors): sorted keys, payloads, bucket sizes, pad counts, the p-1
+splitters, the whole sorted sample and, where marked, the bucket of every key.
+
+  * 2^28 int32 [U], p = 4096, random oversampling, s = 2 lg^2 n = 1568
+    (sample 6,422,527), keys only -- the headline workload;
+  * the same keys, regular oversampling, p = R = s = 4096 (sample 2^24);
+  * 2^28 int32 Zipf(1.1) over 256 values + payload = input index, regular,
+    p = R = s = 4096 (the duplicate-heavy configuration; payload order checks
+    the tie-break of Sec. 5.1.1);
+  * 2^28 float64 Gaussian mixture, p = 4096, random, s = 16, with the
+    splitter tree and with the learned classifier; the learned per-key
+    buckets come from the learned classifier itself.
+
+Seeds are the bench's (keys seed 1, sample seed 1).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import bsp_inputs as gen
+import oracle
+from tests.gpu_util import assert_same, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 28
+P = 4096
+THREADS = max(1, os.cpu_count() or 1)
+
+
+def _oracle(keys, p, s, runs, mode, seed, vals=None, bucket_of=False):
+    return oracle.sort(keys, p, s, runs, mode, seed, vals=vals, want_sample=True,
+                       want_bucket_of=bucket_of, threads=THREADS)
+
+
+@pytest.fixture(scope="module")
+def uniform_keys():
+    return gen.uniform(N, P, 1)
+
+
+def test_headline_uniform_random_2e28(uniform_keys):
+    keys = uniform_keys
+    ref = _oracle(keys, P, 0, 0, oracle.RANDOM, 1, bucket_of=True)
+    gpu = run_gpu(keys, P, 0, 0, oracle.RANDOM, 1, bucket_of=True)
+    assert gpu.plan.s == 1568 and gpu.plan.sample_size == 1568 * P - 1
+    assert_same(gpu, ref)
+    # the paper's observation (Sec. 6.4): maximum imbalance well under 15%
+    assert ref.bucket_sizes.max() < 1.15 * N / P
+
+
+def test_headline_uniform_regular_2e28(uniform_keys):
+    keys = uniform_keys
+    ref = _oracle(keys, P, P, P, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, P, P, P, oracle.REGULAR, 0, bucket_of=False)
+    assert gpu.plan.sample_size == P * P
+    assert_same(gpu, ref)
+
+
+def test_zipf_pairs_regular_2e28():
+    keys = gen.zipf(N, seed=1)
+    vals = np.arange(N, dtype=np.uint32)
+    ref = _oracle(keys, P, P, P, oracle.REGULAR, 0, vals=vals)
+    gpu = run_gpu(keys, P, P, P, oracle.REGULAR, 0, vals, bucket_of=False)
+    assert_same(gpu, ref)
+    # Lemma 5.1 (refined form, x = 16): no bucket above (q + R - 1) x - R + 1 records
+    x, q, R = gpu.plan.M // gpu.plan.s, gpu.plan.s, P
+    assert (ref.bucket_sizes + ref.pad_sizes).max() <= (q + R - 1) * x - R + 1
+
+
+@pytest.fixture(scope="module")
+def gmm_case():
+    keys = gen.gmm(N, seed=1)
+    ref = _oracle(keys, P, 16, 0, oracle.RANDOM, 1, bucket_of=True)
+    return keys, ref
+
+
+@pytest.mark.parametrize("classify", [0, 1], ids=["tree", "learned"])
+def test_gmm_f64_random_2e28(gmm_case, classify):
+    keys, ref = gmm_case
+    gpu = run_gpu(keys, P, 16, 0, oracle.RANDOM, 1, classify=classify, bucket_of=True)
+    assert gpu.plan.sample_size == 16 * P - 1
+    assert_same(gpu, ref)

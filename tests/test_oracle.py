@@ -380,3 +380,32 @@ def test_random_mode_independent_of_virtual_processors():
         assert np.array_equal(r.bucket_sizes, ref.bucket_sizes)
         assert np.array_equal(r.bucket_of, ref.bucket_of)
         assert np.array_equal(r.splitters, ref.splitters)
+
+
+@pytest.mark.parametrize("mode", [oracle.REGULAR, oracle.RANDOM], ids=["regular", "random"])
+@pytest.mark.parametrize("make,p,runs,s", [
+    (lambda: gen.uniform(200_003, 64, 3), 64, 0, 0),
+    (lambda: gen.zipf(150_000, seed=5), 32, 48, 64),
+    (lambda: gen.gmm(100_000, seed=2), 16, 0, 0),
+], ids=["uniform", "zipf", "gmm"])
+def test_threads_run_the_same_supersteps(mode, make, p, runs, s):
+    """The processors of one superstep write disjoint data (BSP model): running
+    them on several host threads changes nothing, bit for bit."""
+    keys = make()
+    vals = np.arange(keys.shape[0], dtype=np.uint32)
+    if mode == oracle.RANDOM:
+        runs, s = 0, 0
+    one = oracle.sort(keys, p, s, runs, mode, 11, vals=vals, want_bucket_of=True, threads=1)
+    many = oracle.sort(keys, p, s, runs, mode, 11, vals=vals, want_bucket_of=True, threads=5)
+    for f in ("keys", "vals", "bucket_sizes", "pad_sizes", "sample", "splitters", "bucket_of"):
+        assert getattr(one, f).tobytes() == getattr(many, f).tobytes(), f
+    order = np.argsort(keys, kind="stable")
+    assert many.keys.tobytes() == keys[order].tobytes()
+    assert np.array_equal(many.vals, order)
+
+
+def test_std_sort_baseline_sorts():
+    """The std::sort / std::stable_sort baseline timed beside the oracle sorts."""
+    for keys in (gen.uniform(100_000, 4, 1), gen.uniform_u32(50_000, 2), gen.gmm(30_000, seed=1)):
+        for stable in (False, True):
+            assert np.array_equal(oracle.std_sort(keys, stable=stable), np.sort(keys))

@@ -45,7 +45,7 @@ def _build(mutant_src, outdir):
     c = os.path.join(outdir, "m.c")
     so = os.path.join(outdir, "m.so")
     open(c, "w").write(mutant_src)
-    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-o", so, c])
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", so, c])
     lib = ctypes.CDLL(so)
     P = ctypes.c_void_p
     lib.oracle_sort.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, ctypes.POINTER(oracle.Params),
