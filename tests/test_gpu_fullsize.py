@@ -31,13 +31,22 @@ N = 1 << 28
 
 
 def _host_gb_available():
+    """Free host memory in GB: MemAvailable, capped by the cgroup's limit."""
+    gb = 0.0
     try:
         for line in open("/proc/meminfo"):
             if line.startswith("MemAvailable:"):
-                return int(line.split()[1]) / 2**20
+                gb = int(line.split()[1]) / 2**20
     except OSError:
         pass
-    return 0.0
+    try:
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        if lim != "max":
+            used = int(open("/sys/fs/cgroup/memory.current").read().strip())
+            gb = min(gb, (int(lim) - used) / 2**30)
+    except (OSError, ValueError):
+        pass
+    return gb
 
 
 # the oracle holds about 24 bytes per key twice (blocks and buckets) at its peak
