@@ -12,6 +12,7 @@
 #include "kernels.cuh"
 #include "segsort.cuh"
 #include "segsort_keys.cuh"
+#include "bucket_keys32.cuh"
 
 namespace bsps {
 
@@ -122,6 +123,36 @@ bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
         return;
     }
     auto emit = [&](uint32_t pos, K key) { out_k[pos] = KeyTraits<DT>::inv(key); };
+    if (!SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
+        if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
+            const int slot = atomicAdd(&a.st->retry_count, 1);
+            a.retry_list[slot] = (uint32_t)v;
+        }
+    }
+}
+
+// Tier 1 for 32-bit keys: the same cluster per sub-bucket, with the lean
+// split / exchange / count sort of bucket_keys32.cuh.
+template <int DT, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
+bucket_keys32_kernel(const BucketArgs<uint32_t> a) {
+    using SS = BucketKeys32<CL>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t v = blockIdx.x / CL;
+    const int64_t cnt = imin64(a.vsize[v], a.cap);
+    if (cnt == 0) return;
+    const uint32_t lo = v > 0 ? a.vphi[v - 1] : (uint32_t)~a.st->ext_min_inv;
+    const uint32_t hi = v < a.P - 1 ? a.vphi[v] : (uint32_t)a.st->ext_max;
+    uint32_t *out_k = a.out_keys + a.voff[v];
+    if (lo == hi) {  // one key value: nothing to read
+        const uint32_t x = KeyTraits<DT>::inv(lo);
+        const int64_t share = (cnt + CL - 1) / CL, e0 = (int64_t)(blockIdx.x % CL) * share;
+        const int64_t e1 = imin64(cnt, e0 + share);
+#pragma unroll 4
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) out_k[e] = x;
+        return;
+    }
+    auto emit = [&](uint32_t pos, uint32_t key) { out_k[pos] = KeyTraits<DT>::inv(key); };
     if (!SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
         if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
             const int slot = atomicAdd(&a.st->retry_count, 1);
@@ -247,15 +278,26 @@ static cudaError_t launch_cluster(const Ctx &c, const BucketArgs<typename KeyTra
 template <int DT, int CL, int ITEMS>
 static cudaError_t launch_keys(const Ctx &c, const BucketArgs<typename KeyTraits<DT>::T> &a) {
     using K = typename KeyTraits<DT>::T;
-    using SS = SegSortKeys<K, CL, ITEMS, false>;
-    // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-    static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024, "two CTAs per SM");
-    const size_t smem = SS::smem_bytes();
-    auto kern = bucket_keys_kernel<DT, CL, ITEMS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(c.pl.P * CL), 512, smem, c.stream>>>(a);
-    return cudaGetLastError();
+    if constexpr (sizeof(K) == 4) {
+        using SS = BucketKeys32<CL>;
+        static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024, "two CTAs per SM");
+        const size_t smem = SS::smem_bytes();
+        auto kern = bucket_keys32_kernel<DT, CL>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)(c.pl.P * CL), 512, smem, c.stream>>>(a);
+        return cudaGetLastError();
+    } else {
+        using SS = SegSortKeys<K, CL, ITEMS, false>;
+        // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+        static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024, "two CTAs per SM");
+        const size_t smem = SS::smem_bytes();
+        auto kern = bucket_keys_kernel<DT, CL, ITEMS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)(c.pl.P * CL), 512, smem, c.stream>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
