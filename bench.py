@@ -50,6 +50,10 @@ WORKLOADS = {
     # captures of the bucket sort
     "uniform_2e27_int32_p2048_random": dict(n=1 << 27, p=2048, sampling=1, s=0, runs=0, pairs=False,
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    # the 2^28 workload's buckets exactly (65,536 keys spanning 2^19 values,
+    # clusters of 8) on half the data: keys uniform on [0, 2^30), p = 2048
+    "uniform30_2e27_int32_p2048_random": dict(n=1 << 27, p=2048, sampling=1, s=0, runs=0, pairs=False,
+                                             make=lambda n, p, seed: gen.uniform(n, p, seed) >> 1),
     # the Zipf pairs configuration on a quarter of the data, for full ncu
     # captures of its kernels
     "zipf_2e26_int32_pairs_p4096_regular": dict(n=1 << 26, p=4096, sampling=0, s=4096, runs=4096, pairs=True,

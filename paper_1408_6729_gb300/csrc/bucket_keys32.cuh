@@ -15,11 +15,12 @@
 //   4. each CTA copies its stage, run by run, to the owners' receive buffers
 //      (st.shared::cluster at a precomputed address per bin);
 //   5. each owner sorts what it received by one counting pass: bins of one
-//      value when the owned range is at most 2^12 values wide; up to 2400
-//      bins of 32 values, where three occupancy masks per bin (values seen
-//      once, twice, three times) place every key whose value occurs at most
-//      three times by popcounts alone; other keys (and every key of a wider
-//      range) are placed by comparison inside their bin;
+//      value when the owned range is below 2^12 values; up to 3600 bins of 32
+//      values, where three occupancy masks per bin (values seen once, twice,
+//      three times) place every key whose value occurs at most three times
+//      by popcounts alone; for wider ranges up to 8192 bins, where keys
+//      sharing a bin (and keys of bins where a value occurs four times) are
+//      placed by comparison;
 //   6. the sorted keys are written to the output range the owner's bins
 //      occupy, which is contiguous.
 // Only when some owner would receive more keys than it holds does the
@@ -41,9 +42,10 @@ struct BucketKeys32 {
     static constexpr int ITEMS = 20;
     static constexpr int CAP = T * ITEMS;            // keys one CTA holds
     static constexpr int R = 256;                    // split bins
-    static constexpr int kMaxBins = 4096;            // count bins
-    static constexpr int kMaskBins = 2400;           // count bins with occupancy masks (32 values each)
+    static constexpr int kMaxBins = 8192;            // count bins
+    static constexpr int kMaskBins = 3600;           // count bins with occupancy masks (32 values each)
     static constexpr uint32_t kBinMax = 64;          // longest count bin ordered by comparison
+    static constexpr uint32_t kListMax = T;          // keys of masked bins placed by comparison
     static constexpr uint32_t kRep = 0x80000000u;    // bin start flag: a value of the bin repeats
     static constexpr uint32_t kLater = 0x40000000u;  // ... and some value occurs four times or more
     static constexpr uint32_t kStart = 0x3fffffffu;
@@ -61,6 +63,7 @@ struct BucketKeys32 {
         uint32_t rpos[R];     // position of bin d's first key among the owned keys
         uint32_t odelta[R];   // received bin d: output position = odelta[d] + sorted position
         K bmin[R], bmax[R];   // smallest / largest key of my share per split bin (flat-bin pass)
+        uint32_t list[kListMax];  // waiting slots of the keys the count sort places by comparison
         uint32_t orecv[CL], ofirst[CL], olast[CL], obase[CL];
         uint32_t tmp[40];
     };
@@ -111,29 +114,26 @@ struct BucketKeys32 {
     // occurrences), their exclusive scan in place, chist[nb] = total, the
     // repeat flag on every bin where some value occurs twice, and the later
     // flag where some value occurs four times or more.
+    template <bool MASKS>
     __device__ static void scan_bins(uint32_t *chist, const uint32_t *m1, const uint32_t *m2, const uint32_t *m3,
-                                     int nb, bool masks, uint32_t *tmp) {
+                                     int nb, uint32_t *tmp) {
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         constexpr int W = T / 32;
-        const int per = (nb + T - 1) / T;  // <= 8
-        const int b0 = tid * per;
-        uint32_t len[8];  // bin length | flags
-        uint32_t s = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            len[q] = 0;
-            const int b = b0 + q;
-            if (q < per && b < nb) {
-                const uint32_t later = chist[b];
-                len[q] = later;
-                if (masks) {
-                    const uint32_t w2 = m2[b];
-                    len[q] += __popc(m1[b]) + __popc(w2) + __popc(m3[b]);
-                    len[q] |= (w2 ? kRep : 0u) | (later ? kLater : 0u);
-                }
-                s += len[q] & kStart;
+        const int per = (nb + T - 1) / T;  // <= 16
+        const int b0 = tid * per, b1 = min(nb, b0 + per);
+        // bin length | flags (read twice rather than held in registers)
+        auto len_of = [&](int b) {
+            const uint32_t later = chist[b];
+            uint32_t len = later;
+            if constexpr (MASKS) {
+                const uint32_t w2 = m2[b];
+                len += __popc(m1[b]) + __popc(w2) + __popc(m3[b]);
+                len |= (w2 ? kRep : 0u) | (later ? kLater : 0u);
             }
-        }
+            return len;
+        };
+        uint32_t s = 0;
+        for (int b = b0; b < b1; ++b) s += len_of(b) & kStart;
         uint32_t wtot;
         const uint32_t wex = warp_excl_scan(s, &wtot);
         if (lane == 31) tmp[warp] = wtot;
@@ -147,30 +147,40 @@ struct BucketKeys32 {
         }
         __syncthreads();
         uint32_t run = tmp[warp] + wex;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int b = b0 + q;
-            if (q < per && b < nb) {
-                chist[b] = run | (len[q] & ~kStart);
-                run += len[q] & kStart;
-            }
+        for (int b = b0; b < b1; ++b) {
+            const uint32_t len = len_of(b);
+            chist[b] = run | (len & ~kStart);
+            run += len & kStart;
         }
         if (tid == 0) chist[nb] = tmp[W];
         __syncthreads();
     }
 
+    // Count-bin regimes of count_sort.
+    enum { kValueBins = 0, kMaskedBins = 1, kSparseBins = 2 };
+
     // Sorts the keys held in registers (where valid(i)), all in
-    // [llo, llo + range], into out[0..n).  scr holds kWordsA words.  Returns
-    // false (uniformly) when a count bin that needs comparisons is too long.
+    // [llo, llo + range], into out[0..n).  scr holds kWordsA words, list
+    // kListMax words.  Returns false (uniformly) when the keys that need
+    // comparisons are too many or sit in too long a bin.
     template <typename Valid>
     __device__ static bool count_sort(const K (&k)[ITEMS], Valid valid, K llo, K range, K *out, uint32_t *scr,
-                                      uint32_t *tmp) {
-        // bins of one value, of 32 values with occupancy masks, or wider
-        // bins placed by comparison
+                                      uint32_t *tmp, uint32_t *list) {
+        // bins of one value (range below 2^12); bins of 32 values with three
+        // occupancy masks (values seen once, twice, three times) when the
+        // range is at most 32 kMaskBins values; else up to kMaxBins bins of
+        // about one key, placed by comparison when they hold more
+        if (range < (K)4096) return count_sort_mode<kValueBins>(k, valid, llo, range, 0, out, scr, tmp, list);
+        if ((range >> 5) < (K)kMaskBins) return count_sort_mode<kMaskedBins>(k, valid, llo, range, 5, out, scr, tmp, list);
         int shift = 0;
-        const bool masks = range >= (K)kMaxBins && (range >> 5) < (K)kMaskBins;
-        if (masks) shift = 5;
-        else while ((range >> shift) >= (K)kMaxBins) ++shift;
+        while ((range >> shift) >= (K)kMaxBins) ++shift;
+        return count_sort_mode<kSparseBins>(k, valid, llo, range, shift, out, scr, tmp, list);
+    }
+
+    template <int MODE, typename Valid>
+    __device__ static bool count_sort_mode(const K (&k)[ITEMS], Valid valid, K llo, K range, int shift, K *out,
+                                           uint32_t *scr, uint32_t *tmp, uint32_t *list) {
+        constexpr bool MASKS = MODE == kMaskedBins;
         const int nb = (int)(range >> shift) + 1;
         uint32_t *chist = scr, *m1 = scr + kMaskOff, *m2 = m1 + kMaskOff, *m3 = m2 + kMaskOff;
         const int tid = threadIdx.x;
@@ -179,107 +189,139 @@ struct BucketKeys32 {
             const uint4 z = make_uint4(0u, 0u, 0u, 0u);
             for (int q = tid * 4; q < nb; q += T * 4) {
                 *reinterpret_cast<uint4 *>(chist + q) = z;
-                if (masks) {
+                if constexpr (MASKS) {
                     *reinterpret_cast<uint4 *>(m1 + q) = z;
                     *reinterpret_cast<uint4 *>(m2 + q) = z;
                     *reinterpret_cast<uint4 *>(m3 + q) = z;
                 }
             }
+            if (tid == 0) tmp[38] = 0;  // keys on the comparison list
         }
         __syncthreads();
-        // Without masks r is the arrival rank inside the bin.  With masks it
-        // is the occurrence of the value (bits 28..29: first, second, third,
-        // later) and, for later ones, their rank among the bin's later
-        // occurrences (bits 0..27), which chist counts.
-        uint32_t r[ITEMS];
+        // Per key a 16-bit word, two to a register.  Without masks it is the
+        // arrival rank inside the bin.  With masks it is the occurrence of the
+        // value (bits 14..15: first, second, third, later) and, for later
+        // ones, their rank among the bin's later occurrences (bits 0..13),
+        // which chist counts.  After placement (sparse bins): the waiting
+        // slot, or 0xffff when final.
+        uint32_t rp[ITEMS / 2];
+        auto get = [&](int i) { return (rp[i >> 1] >> ((i & 1) * 16)) & 0xffffu; };
+        auto put = [&](int i, uint32_t x) {
+            const int sh = (i & 1) * 16;
+            rp[i >> 1] = (rp[i >> 1] & ~(0xffffu << sh)) | (x << sh);
+        };
+#pragma unroll
+        for (int i = 0; i < ITEMS / 2; ++i) rp[i] = 0xffffffffu;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if (valid(i)) {
                 const uint32_t v = k[i] - llo;
                 const uint32_t bb = min(v >> shift, (uint32_t)nb - 1u);
-                if (masks) {
+                if constexpr (MASKS) {
                     const uint32_t bit = 1u << (v & 31u);
                     uint32_t o = 0;
                     if (atomicOr(&m1[bb], bit) & bit) {
-                        o = 1u << 28;
+                        o = 1u << 14;
                         if (atomicOr(&m2[bb], bit) & bit) {
-                            o = 2u << 28;
-                            if (atomicOr(&m3[bb], bit) & bit) o = 3u << 28 | atomicAdd(&chist[bb], 1u);
+                            o = 2u << 14;
+                            if (atomicOr(&m3[bb], bit) & bit) o = 3u << 14 | atomicAdd(&chist[bb], 1u);
                         }
                     }
-                    r[i] = o;
+                    put(i, o);
                 } else {
-                    r[i] = atomicAdd(&chist[bb], 1u);
+                    put(i, atomicAdd(&chist[bb], 1u));
                 }
             }
         __syncthreads();
-        scan_bins(chist, m1, m2, m3, nb, masks, tmp);
+        scan_bins<MASKS>(chist, m1, m2, m3, nb, tmp);
         bool cmp = false;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if (valid(i)) {
                 const uint32_t v = k[i] - llo;
                 const uint32_t bb = min(v >> shift, (uint32_t)nb - 1u);
-                const uint32_t h = chist[bb], b0 = h & kStart;
-                uint32_t pos;
-                bool fin = true;
-                if (masks) {
-                    // keys of smaller values: their first, second and third
-                    // occurrences, then this key's own occurrence
+                const uint32_t h = chist[bb], b0 = h & kStart, r = get(i);
+                if constexpr (MASKS) {
+                    // keys of smaller values (their first, second and third
+                    // occurrences), then this key's own occurrence
                     const uint32_t below = (1u << (v & 31u)) - 1u;
-                    const uint32_t w1 = m1[bb];
-                    pos = b0 + __popc(w1 & below);
-                    if (h & kRep) {
-                        const uint32_t occ = r[i] >> 28;
-                        pos += __popc(m2[bb] & below) + __popc(m3[bb] & below) + occ;
-                        if (h & kLater) {  // some value occurs four times or more
-                            const uint32_t w2 = m2[bb], w3 = m3[bb], later = r[i] & 0x0fffffffu;
-                            const uint32_t c1 = __popc(w1), c12 = c1 + __popc(w2), c123 = c12 + __popc(w3);
-                            if (c1 == 1) {
-                                pos = b0 + (occ < 3 ? occ : 3u + later);  // one value: any distinct slot
-                            } else {
-                                // a distinct waiting slot; the comparisons below place it
-                                fin = false;
-                                pos = b0 + __popc(w1 & below);
-                                if (occ == 1) pos = b0 + c1 + __popc(w2 & below);
-                                else if (occ == 2) pos = b0 + c12 + __popc(w3 & below);
-                                else if (occ == 3) pos = b0 + c123 + later;
-                            }
+                    const uint32_t w1 = m1[bb], w2 = m2[bb], w3 = m3[bb], occ = r >> 14;
+                    uint32_t pos = b0 + __popc(w1 & below) + __popc(w2 & below) + __popc(w3 & below) + occ;
+                    if (h & kLater) {  // some value of the bin occurs four times or more
+                        const uint32_t later = r & 0x3fffu, c1 = __popc(w1);
+                        if (c1 == 1) {
+                            pos = b0 + (occ < 3 ? occ : 3u + later);  // one value: any distinct slot
+                        } else {
+                            // a distinct waiting slot, listed; the comparisons below place it
+                            const uint32_t c12 = c1 + __popc(w2);
+                            pos = b0 + __popc(w1 & below);
+                            if (occ == 1) pos = b0 + c1 + __popc(w2 & below);
+                            else if (occ == 2) pos = b0 + c12 + __popc(w3 & below);
+                            else if (occ == 3) pos = b0 + c12 + __popc(w3) + later;
+                            const uint32_t at = atomicAdd(&tmp[38], 1u);
+                            if (at < kListMax) list[at] = pos;
+                            cmp = true;
                         }
                     }
+                    out[pos] = k[i];
                 } else {
-                    pos = b0 + r[i];
-                    fin = shift == 0 || (chist[bb + 1] & kStart) - b0 == 1;
+                    const uint32_t pos = b0 + r;
+                    const bool fin = MODE == kValueBins || (chist[bb + 1] & kStart) - b0 == 1;
+                    out[pos] = k[i];
+                    put(i, fin ? 0xffffu : pos);
+                    cmp |= !fin;
                 }
-                out[pos] = k[i];
-                r[i] = fin ? 0xffffffffu : pos;
-                cmp |= !fin;
             }
         if (!__syncthreads_or(cmp)) return true;
-        // place = bin start + keys of the bin below k + equal keys stored before it
-        bool too_long = false;
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (valid(i) && r[i] != 0xffffffffu) {
-                const uint32_t bb = min((k[i] - llo) >> shift, (uint32_t)nb - 1u);
-                const uint32_t b0 = chist[bb] & kStart, b1 = chist[bb + 1] & kStart, self = r[i];
-                if (b1 - b0 > kBinMax) {
-                    too_long = true;
-                } else {
-                    uint32_t pos = b0;
-                    for (uint32_t y = b0; y < b1; ++y) {
-                        const K x = out[y];
-                        pos += (x < k[i]) | ((x == k[i]) & (y < self));
-                    }
-                    r[i] = pos;
+        if constexpr (MASKS) {
+            // the listed keys: place = bin start + keys of the bin below the
+            // key + equal keys stored before it (all of the bin's keys wait in
+            // distinct slots of the bin)
+            const uint32_t nl = tmp[38];
+            if (nl > kListMax) return false;  // uniform
+            uint32_t dst = 0xffffffffu;
+            K key = 0;
+            if (tid < (int)nl) {
+                const uint32_t self = list[tid];
+                key = out[self];
+                const uint32_t bb = min((key - llo) >> shift, (uint32_t)nb - 1u);
+                const uint32_t b0 = chist[bb] & kStart, b1 = chist[bb + 1] & kStart;
+                dst = b0;
+                for (uint32_t y = b0; y < b1; ++y) {
+                    const K x = out[y];
+                    dst += (x < key) | ((x == key) & (y < self));
                 }
             }
-        if (__syncthreads_or(too_long)) return false;
+            __syncthreads();
+            if (dst != 0xffffffffu) out[dst] = key;
+            __syncthreads();
+            return true;
+        } else {
+            // place = bin start + keys of the bin below k + equal keys stored before it
+            bool too_long = false;
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i)
-            if (valid(i) && r[i] != 0xffffffffu) out[r[i]] = k[i];
-        __syncthreads();
-        return true;
+            for (int i = 0; i < ITEMS; ++i)
+                if (valid(i) && get(i) != 0xffffu) {
+                    const uint32_t bb = min((k[i] - llo) >> shift, (uint32_t)nb - 1u);
+                    const uint32_t b0 = chist[bb] & kStart, b1 = chist[bb + 1] & kStart, self = get(i);
+                    if (b1 - b0 > kBinMax) {
+                        too_long = true;
+                    } else {
+                        uint32_t pos = b0;
+                        for (uint32_t y = b0; y < b1; ++y) {
+                            const K x = out[y];
+                            pos += (x < k[i]) | ((x == k[i]) & (y < self));
+                        }
+                        put(i, pos);
+                    }
+                }
+            if (__syncthreads_or(too_long)) return false;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i)
+                if (valid(i) && get(i) != 0xffffu) out[get(i)] = k[i];
+            __syncthreads();
+            return true;
+        }
     }
 
     // Sorts the cnt keys at src (16-byte aligned; reading up to the next
@@ -299,7 +341,8 @@ struct BucketKeys32 {
             const int n = (int)cnt;
             load(k, src, n);
             auto mine = [&](int i) { return lidx(i) < n; };
-            if (!count_sort(k, mine, lo, hi - lo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp)) return false;
+            if (!count_sort(k, mine, lo, hi - lo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp, sm.list))
+                return false;
             for (int j = tid; j < n; j += T) emit((uint32_t)j, regB[j]);
             return true;
         } else {
@@ -453,7 +496,7 @@ struct BucketKeys32 {
             auto received = [&](int i) { return slot(i) < got; };
             // a CTA that cannot finish gives the sub-bucket back; what the
             // others emit is rewritten, identically, by the stable sort
-            if (!count_sort(kr, received, llo, lhi - llo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp))
+            if (!count_sort(kr, received, llo, lhi - llo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp, sm.list))
                 return false;
             // 6. out: with no flat bin among mine, one contiguous output range
             if (sm.odelta[first] == sm.odelta[last]) {
