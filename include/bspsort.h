@@ -54,6 +54,7 @@ typedef enum { BSPS_TREE = 0, BSPS_LEARNED = 1 } bsps_classify;
 #define BSPS_ERR_CUDA (-5)
 #define BSPS_ERR_DEVICE_TIMEOUT (-6)
 #define BSPS_ERR_TOO_LARGE (-7)
+#define BSPS_ERR_CAPTURE (-8)  /* bsps_sort_batched: the stream is being captured */
 
 /*
  * Parameters, as the paper states them.
@@ -128,7 +129,15 @@ typedef struct {
  *     the call records on its stream at the phase boundaries: before sampling,
  *     after sampling, after the sample sort, after splitter selection, after
  *     routing, after the bucket sort.
- *   launches: HOST int32 that receives the number of kernels the call launched. */
+ *   launches: HOST int32 that receives the number of kernels the call launched.
+ *   stall_tile, wait_polls: test hooks of the bounded waits (Sec. 5.1: the
+ *     prefix step depends on every earlier processor).  With payloads,
+ *     routing tile stall_tile - 1 never publishes its per-bucket counts
+ *     (0: every tile publishes), so the later tiles' look-back waits on it
+ *     expire; wait_polls bounds the polls of one wait (0: the default bound,
+ *     about a second).  An expired wait records BSPS_ERR_DEVICE_TIMEOUT,
+ *     which bsps_read_stats returns; the call's output is then undefined but
+ *     every access stays inside the caller's buffers. */
 #define BSPS_PHASES 6
 typedef struct {
     bsps_record *sample;     /* plan.sample_size records, sorted */
@@ -139,6 +148,8 @@ typedef struct {
     int32_t *launches;
     float *mlp_params;       /* learned classifier: the 1153 trained parameters */
     float *mlp_loss;         /* learned classifier: training loss before and after */
+    int32_t stall_tile;      /* test hook (see above); 0: none */
+    uint32_t wait_polls;     /* test hook (see above); 0: the default bound */
 } bsps_debug;
 
 /*
@@ -241,11 +252,23 @@ int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y
  * keeps the previous call's contents: the call clears what must start at zero
  * itself, and calls whose executions overlap on the GPU (different streams,
  * or different host threads without ordering) race on it and must not be
- * issued.  Device-side statistics of these calls are not exposed.
+ * issued.  bsps_noalloc_read_stats reads the device-side status and
+ * statistics of the last such call (a bucket overflow or an expired wait
+ * happens on the device, after the call has returned BSPS_OK).
  */
 #define BSPS_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, int64_t n, int32_t dtype,
                            const bsps_params *prm, int64_t *d_bucket_sizes, void *stream);
+
+/*
+ * bsps_noalloc_read_stats -- bsps_read_stats for the no-allocation entry
+ * point: synchronises `stream` and reads the status block at the start of the
+ * library's static scratch on the current device.  Like the sorts that share
+ * that scratch, it must not overlap a bsps_sort_keys_noalloc call running on
+ * another stream.  Returns stats->status (BSPS_ERR_CUDA if the scratch's
+ * address cannot be looked up).
+ */
+int bsps_noalloc_read_stats(bsps_stats *stats, void *stream);
 
 /*
  * ---- Batched sorting: many independent keys-only sorts in one call --------
@@ -269,10 +292,19 @@ int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, int64_t n, i
  * per instance, in one persistent launch (sample, sample sort, splitters,
  * classification, bucket histogram, routing into buckets and the final sort
  * all in shared memory).  The others run the single-instance pipeline on
- * t->lanes streams that fork from and join back into `stream`.  Unless
- * `stream` is already being captured, the call records all of this into one
- * CUDA graph; the instantiated graph is kept and relaunched by later calls
- * with the same arguments (pointers, offsets, parameters, table).
+ * t->lanes streams that fork from and join back into `stream`.  The call
+ * records all of this into one CUDA graph of its own; the instantiated graph
+ * is kept and relaunched by later calls with the same arguments (pointers,
+ * offsets, parameters, table).  Because the call keeps and relaunches its own
+ * graph and uploads the on-chip instances' table from host memory that it
+ * does not keep, it must not itself be captured: on a stream that is being
+ * captured it returns BSPS_ERR_CAPTURE and queues nothing.
+ *
+ * The offsets are a HOST array (not a device one): the size classes, the
+ * split into on-chip instances and pipeline lanes, the workspace layout and
+ * the graph all depend on them and are planned on the host before anything
+ * is queued.  The size-class table t replaces one parameter set per call:
+ * every instance takes the p of its size class.
  *
  * h_offsets: host array of num+1 nondecreasing key offsets, h_offsets[0] = 0.
  * d_bucket_sizes: device int64 array (nullable) of the instances' bucket
@@ -281,7 +313,7 @@ int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, int64_t n, i
  * Keys are 32- or 64-bit (the on-chip path takes 32-bit keys only).
  * Errors: BSPS_ERR_INVALID_ARG (bad offsets, num < 0, in == out, bad table),
  * BSPS_ERR_WORKSPACE_TOO_SMALL, BSPS_ERR_TOO_LARGE (an instance too large
- * for bsps_sort_keys), BSPS_ERR_CUDA.  Device-side statuses of all instances
+ * for bsps_sort_keys), BSPS_ERR_CAPTURE, BSPS_ERR_CUDA.  Device-side statuses of all instances
  * (overflow, timeouts) are merged into the batch status that
  * bsps_read_stats(d_ws, ...) reads.
  */

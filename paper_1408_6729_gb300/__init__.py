@@ -24,10 +24,11 @@ BSPS_ERR_BUCKET_OVERFLOW = -4
 BSPS_ERR_CUDA = -5
 BSPS_ERR_DEVICE_TIMEOUT = -6
 BSPS_ERR_TOO_LARGE = -7
+BSPS_ERR_CAPTURE = -8
 
 EXPORTS = ["bsps_get_plan", "bsps_workspace_size", "bsps_sort_keys", "bsps_sort_pairs",
            "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad",
-           "bsps_sort_keys_noalloc", "bsps_tune_default", "bsps_batch_bucket_base",
+           "bsps_sort_keys_noalloc", "bsps_noalloc_read_stats", "bsps_tune_default", "bsps_batch_bucket_base",
            "bsps_batch_workspace_size", "bsps_sort_batched", "bsps_autotune_workspace_size",
            "bsps_autotune_batched", "bsps_strerror"]
 BSPS_BATCH_CLASSES = 32
@@ -76,7 +77,8 @@ class bsps_debug(ctypes.Structure):
                 ("bucket_of", ctypes.c_void_p), ("pad_sizes", ctypes.c_void_p),
                 ("phase_events", ctypes.POINTER(ctypes.c_void_p)),
                 ("launches", ctypes.POINTER(ctypes.c_int32)),
-                ("mlp_params", ctypes.c_void_p), ("mlp_loss", ctypes.c_void_p)]
+                ("mlp_params", ctypes.c_void_p), ("mlp_loss", ctypes.c_void_p),
+                ("stall_tile", ctypes.c_int32), ("wait_polls", ctypes.c_uint32)]
 
 
 _lib = None
@@ -102,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.bsps_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
     lib.bsps_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, SZ, P]
     lib.bsps_sort_keys_noalloc.argtypes = [P, P, I64, I32, PP, P, P]
+    lib.bsps_noalloc_read_stats.argtypes = [ctypes.POINTER(bsps_stats), P]
     PT, PI64 = ctypes.POINTER(bsps_tune), ctypes.POINTER(ctypes.c_int64)
     lib.bsps_tune_default.argtypes = [PT]
     lib.bsps_batch_bucket_base.argtypes = [PI64, I32, PT, PI64]
@@ -188,6 +191,16 @@ def bsps_sort_keys_noalloc(keys_in, keys_out, n, dtype, params, bucket_sizes, st
                                          _ptr(bucket_sizes), _stream(stream))
 
 
+def bsps_noalloc_read_stats(stream=None) -> bsps_stats:
+    """Status and statistics of the last bsps_sort_keys_noalloc call (synchronises
+    the stream); .status is the device-side status."""
+    st = bsps_stats()
+    rc = load().bsps_noalloc_read_stats(ctypes.byref(st), _stream(stream))
+    if rc == BSPS_ERR_CUDA or rc == BSPS_ERR_INVALID_ARG:
+        raise RuntimeError(f"bsps_noalloc_read_stats: {bsps_strerror(rc)} ({rc})")
+    return st
+
+
 def bsps_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, dtype, params, bucket_sizes, workspace,
                     stream=None) -> int:
     return load().bsps_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), int(n),
@@ -197,11 +210,13 @@ def bsps_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, dtype, params, buck
 
 def bsps_sort_debug(keys_in, vals_in, keys_out, vals_out, n, dtype, params, bucket_sizes, workspace,
                     sample=None, splitters=None, bucket_of=None, pad_sizes=None, phase_events=None,
-                    launches=None, mlp_params=None, mlp_loss=None, stream=None) -> int:
+                    launches=None, mlp_params=None, mlp_loss=None, stall_tile=0, wait_polls=0,
+                    stream=None) -> int:
     """phase_events: BSPS_PHASES recorded torch.cuda.Event objects (or raw handles);
-    launches: a ctypes.c_int32 that receives the number of kernels launched."""
+    launches: a ctypes.c_int32 that receives the number of kernels launched;
+    stall_tile, wait_polls: the test hooks of the bounded waits (include/bspsort.h)."""
     dbg = bsps_debug(_ptr(sample), _ptr(splitters), _ptr(bucket_of), _ptr(pad_sizes), None, None,
-                     _ptr(mlp_params), _ptr(mlp_loss))
+                     _ptr(mlp_params), _ptr(mlp_loss), int(stall_tile), int(wait_polls))
     if phase_events is not None:
         handles = [e if isinstance(e, int) else e.cuda_event for e in phase_events]
         assert len(handles) == BSPS_PHASES and all(handles), "events must exist (record them once first)"

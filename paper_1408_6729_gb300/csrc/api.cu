@@ -362,6 +362,7 @@ const char *bsps_strerror(int status) {
     case BSPS_ERR_CUDA: return "CUDA error";
     case BSPS_ERR_DEVICE_TIMEOUT: return "a bounded device wait expired";
     case BSPS_ERR_TOO_LARGE: return "problem too large for the library's limits (see bsps_get_plan)";
+    case BSPS_ERR_CAPTURE: return "the call cannot be captured into a caller's CUDA graph";
     default: return "unknown status";
     }
 }

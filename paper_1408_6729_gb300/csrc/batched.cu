@@ -404,17 +404,20 @@ int bsps_sort_batched(const void *d_keys_in, void *d_keys_out, const int64_t *h_
     if (nkeys > 0 && (!d_keys_in || !d_keys_out || d_keys_in == d_keys_out)) return BSPS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *ws = (unsigned char *)d_ws;
+    // under a caller's capture the table upload below would become a graph
+    // node reading host memory this call does not keep
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return BSPS_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return BSPS_ERR_CAPTURE;
     std::lock_guard<std::mutex> lock(g_mu);
     LaneSet *L = nullptr;
     if ((rc = lanes_for_device(L))) return rc;
-    // the on-chip instances' table, uploaded on every call
+    // the on-chip instances' table, uploaded on every call (from pageable
+    // memory: the copy has read it when cudaMemcpyAsync returns)
     if (!bp.jobs.empty() &&
         cudaMemcpyAsync(ws + ((sizeof(DevStatus) + 255) & ~size_t(255)), bp.jobs.data(),
                         bp.jobs.size() * sizeof(SmallJob), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return BSPS_ERR_CUDA;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return BSPS_ERR_CUDA;
-    if (cs != cudaStreamCaptureStatusNone) return enqueue_batch(bp, d_keys_in, d_keys_out, dtype, d_bucket_sizes, ws, st, L);
 
     // graph key: every argument the recorded work depends on
     std::vector<unsigned char> key;

@@ -51,3 +51,11 @@ extern "C" int bsps_sort_keys_noalloc(const void *d_keys_in, void *d_keys_out, i
     return bsps_sort_keys(d_keys_in, d_keys_out, n, dtype, prm, d_bucket_sizes, ws,
                           (size_t)BSPS_NOALLOC_SCRATCH_BYTES, stream);
 }
+
+extern "C" int bsps_noalloc_read_stats(bsps_stats *stats, void *stream) {
+    if (!stats) return BSPS_ERR_INVALID_ARG;
+    void *ws = nullptr;
+    const int ra = scratch_address(&ws);
+    if (ra) return ra;
+    return bsps_read_stats(ws, stats, stream);
+}

@@ -41,6 +41,8 @@ template <typename K> struct RouteArgs {
     DevStatus *st;
     const float *mlp_params;     // learned classifier (nullable)
     const MlpNorm *mlp_norm;
+    int64_t stall_tile;          // test hook: tile stall_tile - 1 never publishes (0: none)
+    uint32_t spin_limit;         // polls of one bounded wait
 };
 
 template <typename K> struct RouteFixed {
@@ -182,8 +184,9 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
             // p parallel prefix sums of Fig. 1 step 9 (Lemma 4.2), done as a
             // decoupled look-back over earlier tiles' published counts
             uint32_t *my = a.state + tile * P;
+            const bool publish = tile + 1 != a.stall_tile;
             for (uint32_t b = tid; b < P; b += TH) {
-                st_volatile(&my[b], (tile == 0 ? kFlagP : kFlagA) | run[b]);
+                if (publish) st_volatile(&my[b], (tile == 0 ? kFlagP : kFlagA) | run[b]);
                 if (run[b]) atomicAdd(&a.cursor[b], run[b]);
             }
             if (tile > 0) {
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                         for (int w = 0; w < 8; ++w) {
                             if (done) break;
                             uint32_t x = v[w], polls = 0;
-                            while ((x >> 30) == 0 && ++polls < kSpinLimit) {
+                            while ((x >> 30) == 0 && ++polls < a.spin_limit) {
                                 // after any expired wait, nobody waits any more
                                 if ((polls & 255) == 0 && ld_volatile((const uint32_t *)&a.st->timeouts) != 0) break;
                                 __nanosleep(64);
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                         }
                     }
                     const uint32_t c = run[b];
-                    st_volatile(&my[b], kFlagP | ((excl + c) & kValMask));
+                    if (publish) st_volatile(&my[b], kFlagP | ((excl + c) & kValMask));
                     run[b] = excl;
                     if ((uint64_t)excl + c > (uint64_t)a.cap) {
                         atomicExch(&a.st->overflow, 1);
@@ -406,6 +409,8 @@ template <int DT, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) 
     a.st = c.ly.status;
     a.mlp_params = c.ly.mlp_params;
     a.mlp_norm = c.ly.mlp_norm;
+    a.stall_tile = c.dbg.stall_tile;
+    a.spin_limit = c.dbg.wait_polls ? c.dbg.wait_polls : kSpinLimit;
     const size_t smem = RouteSmemLayout<K, LEARNED>((uint32_t)p.P).total;
     auto kern = route_kernel<DT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

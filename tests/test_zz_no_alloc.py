@@ -58,3 +58,25 @@ def test_noalloc_f64_and_rejects_too_large():
     kout = torch.empty_like(kin)
     rc = bsps.bsps_sort_keys_noalloc(kin, kout, n, bsps.BSPS_I32, prm, None)
     assert rc == bsps.BSPS_ERR_TOO_LARGE
+
+
+def test_noalloc_status_is_readable():
+    """A bucket overflow happens on the device after the call has returned
+    BSPS_OK; bsps_noalloc_read_stats reads it from the static scratch (a
+    capacity of 60% of the mean bucket forces it; every write stays inside
+    the regions).  The next call starts from a clear status."""
+    import torch
+    bsps = lib()
+    n, p = 200_000, 16
+    keys = gen.uniform(n, p, 2)
+    kin = to_dev(keys)
+    kout = torch.empty_like(kin)
+    small = bsps.make_params(p, sampling=1, seed=3, capacity_pct=60)
+    assert bsps.bsps_sort_keys_noalloc(kin, kout, n, bsps.BSPS_I32, small, None) == 0
+    st = bsps.bsps_noalloc_read_stats()
+    assert st.status == bsps.BSPS_ERR_BUCKET_OVERFLOW and st.overflow == 1
+    ok = bsps.make_params(p, sampling=1, seed=3)
+    assert bsps.bsps_sort_keys_noalloc(kin, kout, n, bsps.BSPS_I32, ok, None) == 0
+    st = bsps.bsps_noalloc_read_stats()
+    assert st.status == 0 and st.overflow == 0
+    assert kout.cpu().numpy().tobytes() == np.sort(keys).tobytes()
