@@ -79,16 +79,18 @@ METRIC = "keys/sec and % HBM roofline, 2^28 int32; learned/batched vs plain, bit
 # routing pass reads every key and writes it once (8 B); the bucket sort reads
 # and writes every key once (8 B).  With 4-byte payloads both double.
 PHASES = ["sample", "sample_sort", "splitters", "route", "bucket_sort"]
-PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "bucket_keys_kernel",
+PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "bucket_keys32_kernel",
                 ("route", True): "route_kernel", ("bucket_sort", True): "bucket_sort_kernel"}
+PHASE_KERNEL_F64 = {"bucket_sort": "bucket_keys_kernel"}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
 # ncu capture (profiles/*.md), valid while the kernel source is unchanged:
 # routing from the 2^26-key capture (4096 buckets, as at 2^28), the bucket sort
-# from the 2^27-key capture (65,536-key buckets on clusters of 8, as at 2^28);
+# from the 2^27-key capture on [0, 2^30) (65,536-key buckets spanning 2^19
+# values on clusters of 8, as at 2^28);
 # both kernels stream every key once, so bytes per key carry over to 2^28
 NCU_TRAFFIC = {"route_keys_kernel": ((271.315968e6 + 223.367168e6) / (1 << 26), "ac9e5a62a1b9d446"),
-               "bucket_keys_kernel": ((537.344768e6 + 488.002560e6) / (1 << 27), "6cd642d19cc0c3ba")}
+               "bucket_keys32_kernel": ((537.311488e6 + 487.655424e6) / (1 << 27), "ceb023d4ec9e106a")}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
                                        "paper_1408_6729_gb300/csrc/classify.cuh",
@@ -96,7 +98,11 @@ KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "bucket_sort_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
                                         "paper_1408_6729_gb300/csrc/segsort.cuh"],
                  "bucket_keys_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
-                                        "paper_1408_6729_gb300/csrc/segsort_keys.cuh"]}
+                                        "paper_1408_6729_gb300/csrc/segsort_keys.cuh"],
+                 "bucket_keys32_kernel": ["paper_1408_6729_gb300/csrc/bucket.cu",
+                                          "paper_1408_6729_gb300/csrc/bucket_keys32.cuh",
+                                          "paper_1408_6729_gb300/csrc/segsort_keys.cuh",
+                                          "paper_1408_6729_gb300/csrc/radix.cuh"]}
 
 
 def peaks():
@@ -488,6 +494,8 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     kb = key_bytes + (4 if wl["pairs"] else 0)
     dom = max(("route", "bucket_sort"), key=lambda k: per_step[k])
     kern = PHASE_KERNEL[(dom, bool(wl["pairs"]))]
+    if key_bytes == 8 and not wl["pairs"]:
+        kern = PHASE_KERNEL_F64.get(dom, kern)
     alg_bytes = n * 2 * kb
     achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
     traffic = None
