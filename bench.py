@@ -63,8 +63,13 @@ WORKLOADS = {
                                            make=lambda n, p, seed: gen.uniform(n, p, seed)),
     # learned classifier against the splitter tree: 2^28 float64 keys of an
     # 8-component Gaussian mixture (Dirichlet(0.3) weights), p = 4096, s = 16
+    # (both classifiers with the same plan: two sub-buckets per bucket)
     "gmm_2e28_f64_p4096_random_learned": dict(n=1 << 28, p=4096, sampling=1, s=16, runs=0, pairs=False,
-                                             dtype="f64", classify=1, compare="tree",
+                                             dtype="f64", classify=1, compare="tree", refine=2,
+                                             make=lambda n, p, seed: gen.gmm(n, seed=seed)),
+    # the same on a quarter of the data, for ncu captures of the two routings
+    "gmm_2e26_f64_p4096_random_learned": dict(n=1 << 26, p=4096, sampling=1, s=16, runs=0, pairs=False,
+                                             dtype="f64", classify=1, compare="tree", refine=1,
                                              make=lambda n, p, seed: gen.gmm(n, seed=seed)),
     # batched: 20,000 int32 instances, sizes log-uniform on [2^8, 2^22],
     # alternately uniform [U] and Zipf(1.1) over 256 values; the first
@@ -305,7 +310,7 @@ def run_gpu(args, wl, name):
     f64 = wl.get("dtype") == "f64"
     code = bsps.BSPS_F64 if f64 else bsps.BSPS_I32
     prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
-                           refine=args.refine, classify=wl.get("classify", 0))
+                           refine=args.refine or wl.get("refine", 0), classify=wl.get("classify", 0))
     plan = bsps.bsps_get_plan(n, code, prm, wl["pairs"])
     keys_h = np.ascontiguousarray(wl["make"](n, p, 1 + rank))
     kin = torch.from_numpy(keys_h).to(dev)
@@ -405,7 +410,7 @@ def compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st_learned, st
     """The same sort with the splitter tree: time, and identical output."""
     import torch
     prm = bsps.make_params(wl["p"], s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
-                           refine=args.refine, classify=0)
+                           refine=args.refine or wl.get("refine", 0), classify=0)
     plan = bsps.bsps_get_plan(n, code, prm, False)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=kin.device)
     out = torch.empty_like(kout)

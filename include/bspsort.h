@@ -215,20 +215,32 @@ int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream);
 /*
  * Learned classifier (params.classify = BSPS_LEARNED; not in the paper).  A
  * 1->32->32->1 ReLU network (FP32) fits the empirical CDF of the sorted sample
- * the method draws: it starts as the piecewise-linear interpolant of up to
- * 4096 sample points at 33 knots and its output layer is then trained by
- * full-batch gradient descent on the GPU.  It predicts each key's sub-bucket
- * as floor(P * y), and a bounded search against the true splitters corrects
- * every prediction, so all results equal those of BSPS_TREE.  Parameters are packed
- * as W1[32] b1[32] W2[32][32] (row i = unit i of layer 2) b2[32] w3[32] b3.
+ * the method draws (Fig. 3 step 4 / Fig. 1 step 4): it starts as the
+ * piecewise-linear interpolant of up to 4096 sample points at 33 knots and is
+ * then trained on the GPU by full-batch Adam steps on all of its parameters
+ * (the forward and backward pass behind bsps_mlp_loss_grad), keeping the
+ * parameters of the lowest loss.  It is evaluated exactly in its
+ * piecewise-affine form: between two consecutive knots of layer 1, layer 2's
+ * pre-activations are an affine function of the input.  Its output indexes a
+ * table counting, per output cell, the splitters whose own output lies below
+ * the cell; a key's bucket is searched among the splitters of its cell and
+ * checked against the splitters just outside, so all results equal those of
+ * BSPS_TREE whatever the network predicts.  Parameters are packed as W1[32]
+ * b1[32] W2[32][32] (row i = unit i of layer 2) b2[32] w3[32] b3.
  *
  * bsps_mlp_loss_grad -- mean squared error of the network `d_params` on the m
  * points (d_x[i], d_y[i]) and its gradient (1153 floats into d_grad; loss into
  * d_loss, nullable).  Workspace: bsps_mlp_workspace_size(m) bytes.
+ *
+ * bsps_mlp_predict -- the network's output for m inputs d_x (device floats)
+ * into d_y, through the piecewise-affine evaluation the classifier uses.
+ * Workspace: bsps_mlp_workspace_size(0) bytes, 16-byte aligned.
  */
 int bsps_mlp_workspace_size(int64_t m, size_t *bytes);
 int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_y, int64_t m, float *d_grad,
                        float *d_loss, void *d_ws, size_t ws_bytes, void *stream);
+int bsps_mlp_predict(const float *d_params, const float *d_x, int64_t m, float *d_y, void *d_ws, size_t ws_bytes,
+                     void *stream);
 
 /*
  * bsps_sort_keys_noalloc -- bsps_sort_keys without a caller workspace.

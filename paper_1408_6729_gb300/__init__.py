@@ -27,7 +27,7 @@ BSPS_ERR_TOO_LARGE = -7
 BSPS_ERR_CAPTURE = -8
 
 EXPORTS = ["bsps_get_plan", "bsps_workspace_size", "bsps_sort_keys", "bsps_sort_pairs",
-           "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad",
+           "bsps_sort_debug", "bsps_read_stats", "bsps_mlp_workspace_size", "bsps_mlp_loss_grad", "bsps_mlp_predict",
            "bsps_sort_keys_noalloc", "bsps_noalloc_read_stats", "bsps_tune_default", "bsps_batch_bucket_base",
            "bsps_batch_workspace_size", "bsps_sort_batched", "bsps_autotune_workspace_size",
            "bsps_autotune_batched", "bsps_strerror"]
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.bsps_read_stats.argtypes = [P, ctypes.POINTER(bsps_stats), P]
     lib.bsps_mlp_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
     lib.bsps_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, SZ, P]
+    lib.bsps_mlp_predict.argtypes = [P, P, I64, P, P, SZ, P]
     lib.bsps_sort_keys_noalloc.argtypes = [P, P, I64, I32, PP, P, P]
     lib.bsps_noalloc_read_stats.argtypes = [ctypes.POINTER(bsps_stats), P]
     PT, PI64 = ctypes.POINTER(bsps_tune), ctypes.POINTER(ctypes.c_int64)
@@ -239,6 +240,11 @@ def bsps_mlp_workspace_size(m) -> int:
 def bsps_mlp_loss_grad(params, x, y, m, grad, loss, workspace, stream=None) -> int:
     return load().bsps_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), int(m), _ptr(grad), _ptr(loss),
                                      _ptr(workspace), _nbytes(workspace), _stream(stream))
+
+
+def bsps_mlp_predict(params, x, m, y, workspace, stream=None) -> int:
+    return load().bsps_mlp_predict(_ptr(params), _ptr(x), int(m), _ptr(y), _ptr(workspace), _nbytes(workspace),
+                                   _stream(stream))
 
 
 def _offsets(offsets):

@@ -88,10 +88,19 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     pl.B = B;
     pl.P = pl.p * B;
     // the routing kernel keeps two words per sub-bucket in shared memory:
-    // refine less (larger sub-buckets go to the slower sort tiers) if needed
+    // refine less (larger sub-buckets go to the slower sort tiers) if needed,
+    // and also while its splitters would have to stay in global memory, as
+    // long as the expected sub-bucket stays within 2.5 clusters' capacity
     while (prm->refine == 0 && pl.B > 1 && route_smem_bytes(pl) > 227 * 1024) {
         pl.B /= 2;
         pl.P = pl.p * pl.B;
+    }
+    while (prm->refine == 0 && pl.B > 1 && !pl.pairs && !route_keys_splitters_in_smem(pl)) {
+        Plan half = pl;
+        half.B /= 2;
+        half.P = half.p * half.B;
+        if ((double)n / half.P * headroom(half.B) > 2.5 * 8.0 * cap_cta) break;
+        pl = half;
     }
     B = pl.B;
     if (pl.P > 65535) return BSPS_ERR_TOO_LARGE;  // 16-bit sub-bucket ids
@@ -154,6 +163,10 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         take(kMlpPointsMax * 4); take(kMlpPointsMax * 4);
         take(8);
         take(sizeof(MlpNorm));
+        take((int64_t)mlp_opt_bytes());
+        take(sizeof(MlpTables));
+        take(std::max<int64_t>(pl.P, 1) * 4);
+        take((kYCells + 2) * 2);
     }
     pl.ws_bytes = (size_t)o;
     return BSPS_OK;
@@ -195,10 +208,18 @@ static Layout make_layout(const Plan &pl, void *ws) {
         l.mlp_y = (float *)take(kMlpPointsMax * 4);
         l.mlp_npts = (int64_t *)take(8);
         l.mlp_norm = (MlpNorm *)take(sizeof(MlpNorm));
+        l.mlp_opt = take((int64_t)mlp_opt_bytes());
+        l.mlp_tables = (MlpTables *)take(sizeof(MlpTables));
+        l.mlp_ysplit = (float *)take(std::max<int64_t>(pl.P, 1) * 4);
+        l.ylut = (uint16_t *)take((kYCells + 2) * 2);
     } else {
         l.mlp_params = l.mlp_part = l.mlp_x = l.mlp_y = nullptr;
         l.mlp_npts = nullptr;
         l.mlp_norm = nullptr;
+        l.mlp_opt = nullptr;
+        l.mlp_tables = nullptr;
+        l.mlp_ysplit = nullptr;
+        l.ylut = nullptr;
     }
     return l;
 }
@@ -221,7 +242,7 @@ static int kernels_per_call(const Plan &pl) {
     k += 2;                                      // splitters, radix index
     k += 2;                                      // routing, bucket offsets
     k += 3;                                      // copy or keys-only tier, cluster sort, out-of-core sort
-    if (pl.classify == BSPS_LEARNED) k += 4;     // training set, spline start, features, output-layer steps
+    if (pl.classify == BSPS_LEARNED) k += mlp_train_kernels();  // training set, start, Adam steps, tables, index
     return k;
 }
 

@@ -88,10 +88,14 @@ struct Layout {
     uint32_t *run_retry;    // R: blocks the keys-only block sort gave back
     // learned classifier (classify == BSPS_LEARNED)
     float *mlp_params;                   // 1153
-    float *mlp_part;                     // layer-2 features of the training points (points x 32)
+    float *mlp_part;                     // partial gradients of the training CTAs
     float *mlp_x, *mlp_y;                // training points
     int64_t *mlp_npts;
     struct MlpNorm *mlp_norm;
+    void *mlp_opt;                       // Adam state
+    struct MlpTables *mlp_tables;        // the trained network's evaluation form
+    float *mlp_ysplit;                   // the network's output for every splitter
+    uint16_t *ylut;                      // index over the network's output (kYCells + 1)
     void *reg_keys;         // P * cap keys (phi), region v at v*cap
     uint32_t *reg_vals;     // P * cap payloads
     uint32_t *vsize;        // P sub-bucket sizes
@@ -122,7 +126,10 @@ cudaError_t launch_splitters(const Ctx &c);       // Fig. 1 steps 6-7
 cudaError_t launch_route(const Ctx &c);           // Fig. 1 steps 9-11
 cudaError_t launch_bucket_sort(const Ctx &c);     // Fig. 2 step 12
 cudaError_t launch_debug(const Ctx &c);           // optional diagnostics
-cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, spline start, training
+cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, spline start, training,
+                                                  // evaluation tables and the index over its output
+int mlp_train_kernels();                          // kernels launch_mlp_train queues
+size_t mlp_opt_bytes();
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);
@@ -130,5 +137,6 @@ bool msd_sample_sort(const Plan &p);
 int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)               // MSD sample sort is launched (32-bit keys, large samples)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
 size_t route_keys_smem_bytes(const Plan &pl);
+bool route_keys_splitters_in_smem(const Plan &pl);  // keys-only routing holds the splitters on chip
 
 } // namespace bsps

@@ -1,8 +1,8 @@
-// mlp.cu -- training of the learned bucket classifier on the GPU: the training
-// set from the sorted sample, the spline start, the layer-2 features of every
-// training point, and full-batch gradient steps on the output layer; plus the
-// loss and gradient of the whole network (forward and backward written out)
-// behind the entry point that checks them against the CPU oracle.
+// mlp.cu -- the learned bucket classifier on the GPU: the training set from
+// the sorted sample, the spline start, full-batch Adam steps on every
+// parameter (the forward and backward pass of mlp_cta_grad, checked against
+// the CPU oracle through bsps_mlp_loss_grad), the evaluation tables of the
+// trained network, and the index over the splitters' outputs.
 #include <algorithm>
 
 #include "mlp.cuh"
@@ -11,12 +11,14 @@ namespace bsps {
 
 constexpr int kMlpThreads = 128;       // one training point per thread per step
 constexpr int kMlpMaxPoints = kMlpPointsMax;
-constexpr int kMlpSteps = 16;          // gradient steps from the spline start
-// Full-batch gradient descent on the output layer (w3, b3): the loss is a
-// convex quadratic there with Hessian 2 E[h h^T], h = (h2, 1), whose largest
-// eigenvalue is at most 2 * 33 for inputs in [0, 1]; a step below 2/66
-// lowers the loss at every step.
-constexpr float kMlpLr = 0.02f;
+// Full-batch Adam on all 1153 parameters from the spline start.  Each
+// parameter's step is relative to its own scale: a layer-1 bias moves its
+// knot, so its scale is the gap to the nearest other knot (knots inside a
+// narrow mode of the keys are 1e-5 apart, output slopes reach thousands);
+// the other parameters scale with their magnitude.  The parameters of the
+// lowest loss seen are kept.
+constexpr int kMlpSteps = 8;
+constexpr float kMlpLr = 5e-4f;        // step, relative to the parameter's scale
 constexpr int kMlpTrainPoints = 4096;  // training points drawn from the sorted sample
 
 // Per-CTA gradient of the mean squared error over the CTA's points
@@ -105,87 +107,6 @@ __device__ float mlp_cta_grad(const float *w, const float *__restrict__ x, const
 
 constexpr int kMlpScratchFloats = 4 * kMlpThreads * 33 + 2 * kMlpThreads + 8;
 
-// Layers 1 and 2 stay at their start; their output for every training point
-// is computed once.  h2 holds kH x npts floats (feature-major, so that the
-// training steps read consecutive points).
-__global__ void __launch_bounds__(kMlpThreads) mlp_features_kernel(const float *params, const float *x,
-                                                                  const int64_t *npts, float *h2) {
-    __shared__ float w[kParams + 3];
-    for (int k = threadIdx.x; k < kParams; k += kMlpThreads) w[k] = params[k];
-    __syncthreads();
-    const int64_t m = *npts;
-    for (int64_t p = (int64_t)blockIdx.x * kMlpThreads + threadIdx.x; p < m; p += (int64_t)gridDim.x * kMlpThreads) {
-        const float xi = x[p];
-        float h1[kH];
-#pragma unroll
-        for (int j = 0; j < kH; ++j) h1[j] = fmaxf(fmaf(w[kW1 + j], xi, w[kB1 + j]), 0.0f);
-        for (int i = 0; i < kH; ++i) {
-            float z = w[kB2 + i];
-#pragma unroll
-            for (int j = 0; j < kH; ++j) z = fmaf(w[kW2 + i * kH + j], h1[j], z);
-            h2[(int64_t)i * m + p] = fmaxf(z, 0.0f);
-        }
-    }
-}
-
-// Full-batch gradient descent on the output layer (w3, b3) from the cached
-// features, one CTA: every step sums 2 r h2 / m and 2 r / m over the points
-// (r = y - target) and moves w3, b3 against them.  Records the loss before the
-// first step and after the last.
-constexpr int kMlpHeadThreads = 1024;
-__global__ void __launch_bounds__(kMlpHeadThreads) mlp_head_kernel(float *params, const float *h2, const float *y,
-                                                                   const int64_t *npts, int steps, float lr,
-                                                                   float *loss_first, float *loss_last) {
-    constexpr int W = kMlpHeadThreads / 32, NV = kH + 2;  // w3 gradient, b3 gradient, loss
-    __shared__ float head[kH + 1];
-    __shared__ float part[W][NV];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t m = *npts;
-    if (m == 0) return;
-    if (t <= kH) head[t] = params[kW3 + t];  // w3[0..31], b3
-    __syncthreads();
-    for (int step = 0; step <= steps; ++step) {
-        float g[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) g[i] = 0.0f;
-        for (int64_t p = t; p < m; p += kMlpHeadThreads) {
-            float f[kH];
-#pragma unroll
-            for (int i = 0; i < kH; ++i) f[i] = h2[(int64_t)i * m + p];
-            float out = head[kH];
-#pragma unroll
-            for (int i = 0; i < kH; ++i) out = fmaf(head[i], f[i], out);
-            const float r = out - y[p];
-            const float dy = 2.0f * r / (float)m;
-#pragma unroll
-            for (int i = 0; i < kH; ++i) g[i] = fmaf(dy, f[i], g[i]);
-            g[kH] += dy;
-            g[kH + 1] = fmaf(r, r, g[kH + 1]);
-        }
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g[i] += __shfl_xor_sync(0xffffffffu, g[i], o);
-        }
-        if (lane == 0)
-#pragma unroll
-            for (int i = 0; i < NV; ++i) part[warp][i] = g[i];
-        __syncthreads();
-        if (t < NV) {
-            float tot = 0.0f;
-            for (int q = 0; q < W; ++q) tot += part[q][t];
-            if (t == kH + 1) {
-                if (step == 0 && loss_first) *loss_first = tot / (float)m;
-                if (step == steps && loss_last) *loss_last = tot / (float)m;
-            } else if (step < steps) {
-                head[t] -= lr * tot;  // t < kH: w3[t]; t == kH: b3
-            }
-        }
-        __syncthreads();
-    }
-    if (t <= kH) params[kW3 + t] = head[t];
-}
-
 // Loss and gradient only (for the gradient check against the CPU oracle).
 __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(const float *params, const float *x, const float *y,
                                                                int64_t m, float *part) {
@@ -198,6 +119,305 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(const float *para
     float *pp = part + (int64_t)blockIdx.x * (kParams + 1);
     const float lp = mlp_cta_grad(w, x, y, p0, np, m, pp, scratch);
     if (threadIdx.x == 0) pp[kParams] = lp;
+}
+
+// One training step's partial gradients: as mlp_grad_kernel, with the point
+// count read from the device (CTAs past it contribute zeros).
+__global__ void __launch_bounds__(kMlpThreads) mlp_step_grad_kernel(const float *params, const float *x,
+                                                                    const float *y, const int64_t *npts,
+                                                                    float *part) {
+    __shared__ float w[kParams + 3];
+    __shared__ float scratch[kMlpScratchFloats];
+    for (int k = threadIdx.x; k < kParams; k += kMlpThreads) w[k] = params[k];
+    __syncthreads();
+    const int64_t m = *npts;
+    const int64_t p0 = (int64_t)blockIdx.x * kMlpThreads;
+    float *pp = part + (int64_t)blockIdx.x * (kParams + 1);
+    if (p0 >= m) {
+        for (int k = threadIdx.x; k <= kParams; k += kMlpThreads) pp[k] = 0.0f;
+        return;
+    }
+    const int np = (int)imin64(kMlpThreads, m - p0);
+    const float lp = mlp_cta_grad(w, x, y, p0, np, m, pp, scratch);
+    if (threadIdx.x == 0) pp[kParams] = lp;
+}
+
+// Adam state: first and second moments, the best parameters and their loss.
+struct MlpOpt {
+    float m[kParams], v[kParams], best[kParams], scale[kParams], start[kParams];
+    float best_loss;
+    float first_loss;
+};
+
+// Sums the G partial gradients and losses of the current parameters, keeps
+// them as the best if their loss is the lowest so far, and (unless `last`)
+// takes one Adam step; after the last evaluation the best parameters are
+// written back.
+__global__ void __launch_bounds__(1024) mlp_adam_kernel(float *params, const float *part, int G,
+                                                        const int64_t *npts, MlpOpt *opt, int step, int last,
+                                                        float *loss_first, float *loss_last) {
+    __shared__ float s_loss;
+    const int t = threadIdx.x;
+    const int64_t m = *npts;
+    if (m == 0) return;
+    if (t == 0) {
+        float l = 0.0f;
+        for (int c = 0; c < G; ++c) l += part[(int64_t)c * (kParams + 1) + kParams];
+        s_loss = l / (float)m;
+    }
+    __syncthreads();
+    const float loss = s_loss;
+    const bool better = step == 0 || loss < opt->best_loss;
+    if (step == 0) {  // step scales of the parameters, from the start (kept too)
+        for (int k = t; k < kParams; k += 1024) {
+            opt->scale[k] = fmaxf(fabsf(params[k]), 1e-3f);
+            opt->start[k] = params[k];
+        }
+        __syncthreads();
+        if (t < kH) {
+            const float w = params[kW1 + t];
+            if (w != 0.0f) {
+                const float tj = -params[kB1 + t] / w;
+                float gap = 1.0f;
+                for (int j = 0; j < kH; ++j) {
+                    const float wj = params[kW1 + j];
+                    if (j != t && wj != 0.0f) gap = fminf(gap, fabsf(-params[kB1 + j] / wj - tj));
+                }
+                opt->scale[kB1 + t] = fmaxf(gap * fabsf(w), 1e-7f);
+            }
+        }
+        __syncthreads();
+    }
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-12f;
+    const float c1 = 1.0f - powf(b1, (float)(step + 1)), c2 = 1.0f - powf(b2, (float)(step + 1));
+    for (int k = t; k < kParams; k += 1024) {
+        const float p = params[k];
+        if (better) opt->best[k] = p;
+        if (last) continue;
+        float g = 0.0f;
+        for (int c = 0; c < G; ++c) g += part[(int64_t)c * (kParams + 1) + k];
+        const float mk = step == 0 ? (1.0f - b1) * g : b1 * opt->m[k] + (1.0f - b1) * g;
+        const float vk = step == 0 ? (1.0f - b2) * g * g : b2 * opt->v[k] + (1.0f - b2) * g * g;
+        opt->m[k] = mk;
+        opt->v[k] = vk;
+        const float upd = (mk / c1) / (sqrtf(vk / c2) + eps);
+        params[k] = p - kMlpLr * opt->scale[k] * upd;
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (better) opt->best_loss = loss;
+        if (step == 0) {
+            opt->first_loss = loss;
+            if (loss_first) *loss_first = loss;
+        }
+    }
+    if (last) {
+        __syncthreads();
+        for (int k = t; k < kParams; k += 1024) params[k] = opt->best[k];
+        if (t == 0 && loss_last) *loss_last = opt->best_loss;
+    }
+}
+
+// The piecewise-linear form of the network `params` (see MlpTables), in
+// double.  Thread k < 33 takes layer 1's interval k (between its sorted knots
+// k-1 and k): it forms layer 2's affine pre-activations there, cuts the
+// interval where any of them crosses zero, and gives every piece its anchor,
+// value and slope; the pieces of all intervals are then written in order.
+// A network of more than kMlpPieces pieces is replaced by `fallback` (the
+// spline start, at most 33 pieces), when given.
+__global__ void __launch_bounds__(64) mlp_tables_kernel(const float *params_in, const float *fallback,
+                                                        const MlpNorm *norm, MlpTables *T) {
+    __shared__ double knots[kH];
+    __shared__ int nk;
+    __shared__ float s_x[kMlpPiecesAll], s_y[kMlpPiecesAll], s_s[kMlpPiecesAll];
+    __shared__ int s_n[kH + 1], s_off[kH + 2];
+    const int t = threadIdx.x;
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+    const float *params = params_in;
+  again:
+    if (t == 0) {
+        int c = 0;
+        for (int j = 0; j < kH; ++j) {
+            const double w = params[kW1 + j];
+            if (w != 0.0) {  // insertion into the sorted list
+                const double v = -(double)params[kB1 + j] / w;
+                int q = c++;
+                while (q > 0 && knots[q - 1] > v) { knots[q] = knots[q - 1]; --q; }
+                knots[q] = v;
+            }
+        }
+        nk = c;
+    }
+    __syncthreads();
+    const int c = nk;
+    if (t <= c) {
+        const int k = t;
+        const double lo = k == 0 ? -INF : knots[k - 1], hi = k == c ? INF : knots[k];
+        // a point inside the interval decides which layer-1 units are on
+        double xm = 0.0;
+        if (c > 0) xm = k == 0 ? knots[0] - 1.0 : (k == c ? knots[c - 1] + 1.0 : 0.5 * (lo + hi));
+        double A[kH], B[kH];
+        for (int i = 0; i < kH; ++i) {
+            double a = params[kB2 + i], b = 0.0;
+            for (int j = 0; j < kH; ++j) {
+                const double w1 = params[kW1 + j], b1 = params[kB1 + j];
+                if (w1 * xm + b1 > 0.0) {
+                    const double w2 = params[kW2 + i * kH + j];
+                    a += w2 * b1;
+                    b += w2 * w1;
+                }
+            }
+            A[i] = a;
+            B[i] = b;
+        }
+        // cut points inside (lo, hi): zeros of the pre-activations
+        double cuts[kH + 1];
+        int m = 0;
+        for (int i = 0; i < kH; ++i)
+            if (B[i] != 0.0) {
+                const double z = -A[i] / B[i];
+                if (z > lo && z < hi) {
+                    int q = m++;
+                    while (q > 0 && cuts[q - 1] > z) { cuts[q] = cuts[q - 1]; --q; }
+                    cuts[q] = z;
+                }
+            }
+        // piece r of the interval: [left_r, right_r)
+        const int base = k * (kH + 1);
+        for (int r = 0; r <= m; ++r) {
+            const double left = r == 0 ? lo : cuts[r - 1], right = r == m ? hi : cuts[r];
+            double mid, anchor;
+            if (left == -INF && right == INF) { mid = 0.0; anchor = 0.0; }
+            else if (left == -INF) { mid = right - 1.0; anchor = right; }
+            else if (right == INF) { mid = left + 1.0; anchor = left; }
+            else { mid = 0.5 * (left + right); anchor = left; }
+            double y = params[kB3], sl = 0.0;
+            for (int i = 0; i < kH; ++i)
+                if (A[i] + B[i] * mid > 0.0) {
+                    const double w3 = params[kW3 + i];
+                    y += w3 * (A[i] + B[i] * anchor);
+                    sl += w3 * B[i];
+                }
+            s_x[base + r] = (float)anchor;
+            s_y[base + r] = (float)y;
+            s_s[base + r] = (float)sl;
+        }
+        s_n[k] = m + 1;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int o = 0;
+        for (int k = 0; k <= c; ++k) { s_off[k] = o; o += s_n[k]; }
+        s_off[c + 1] = o;
+    }
+    __syncthreads();
+    if (s_off[c + 1] > kMlpPieces && fallback && params != fallback) {  // uniform
+        params = fallback;
+        __syncthreads();
+        goto again;
+    }
+    if (t == 0) {
+        const int o = min(s_off[c + 1], kMlpPieces);
+        int npad = 1;
+        while (npad < o) npad <<= 1;  // cut points: o - 1 < npad
+        T->npieces = o;
+        T->npad = npad;
+        if (norm) T->norm = *norm;
+        // values at the pieces' anchors, made nondecreasing; monotone if no
+        // slope is negative (then the running maximum only absorbs rounding)
+        bool mono = true;
+        for (int k = 0; k <= c; ++k)
+            for (int r = 0; r < s_n[k]; ++r) mono &= s_s[k * (kH + 1) + r] >= 0.0f;
+        if (mono) {
+            float run = -__int_as_float(0x7f800000);
+            for (int k = 0; k <= c; ++k)
+                for (int r = 0; r < s_n[k]; ++r) {
+                    const int q = k * (kH + 1) + r;
+                    run = fmaxf(run, s_y[q]);
+                    s_y[q] = run;
+                }
+        }
+        T->monotone = mono ? 1 : 0;
+    }
+    __syncthreads();
+    if (t <= c) {
+        const int k = t, o = s_off[k];
+        for (int r = 0; r < s_n[k] && o + r < kMlpPieces; ++r) {
+            const int q = k * (kH + 1) + r;
+            // the value at the piece's right end: the next piece's anchor value
+            float yhi = __int_as_float(0x7f800000);
+            if (r + 1 < s_n[k]) yhi = s_y[q + 1];
+            else if (k < c) yhi = s_y[(k + 1) * (kH + 1)];
+            T->piece[o + r] = make_float4(s_x[q], s_y[q], s_s[q], yhi);
+            // left end of every piece but the first: the interval's knot or a cut
+            if (o + r > 0) T->cut[o + r - 1] = r == 0 ? (float)knots[k - 1] : s_x[q];
+        }
+    }
+    __syncthreads();
+    const int np = min(s_off[c + 1], kMlpPieces);
+    for (int q = np - 1 + t; q < kMlpCutsPad; q += 64) T->cut[q] = __int_as_float(0x7f800000);
+}
+
+// The network's output for every splitter (S_{j+1} at index j).
+template <int DT>
+__global__ void mlp_ysplit_kernel(const MlpTables *T, const typename KeyTraits<DT>::T *vphi, int64_t nsplit,
+                                  float *ys) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nsplit) ys[j] = mlp_eval(*T, mlp_input<DT>(KeyTraits<DT>::inv(vphi[j]), T->norm));
+}
+
+// The index over the network's output: ylut[c] = number of splitters whose
+// output cell (after a running maximum over the splitters, so that the
+// counts grow with c) is below c, for c = 0 .. kYCells.
+__global__ void __launch_bounds__(1024) mlp_ylut_kernel(float *ys, int64_t nsplit, uint16_t *ylut) {
+    __shared__ float tmp[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // running maximum, in place: 1024 threads over consecutive slices
+    const int64_t per = (nsplit + 1023) / 1024;
+    const int64_t j0 = (int64_t)t * per, j1 = imin64(nsplit, j0 + per);
+    float mx = -__int_as_float(0x7f800000);
+    for (int64_t j = j0; j < j1; ++j) mx = fmaxf(mx, ys[j]);
+    float run = mx;  // inclusive max scan over threads
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float v = __shfl_up_sync(0xffffffffu, run, o);
+        if (lane >= o) run = fmaxf(run, v);
+    }
+    if (lane == 31) tmp[warp] = run;
+    __syncthreads();
+    if (warp == 0) {
+        float v = tmp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v = fmaxf(v, u);
+        }
+        tmp[lane] = v;
+    }
+    __syncthreads();
+    float pre = warp > 0 ? tmp[warp - 1] : -__int_as_float(0x7f800000);
+    const float excl = __shfl_up_sync(0xffffffffu, run, 1);
+    if (lane > 0) pre = fmaxf(pre, excl);
+    for (int64_t j = j0; j < j1; ++j) {
+        pre = fmaxf(pre, ys[j]);
+        ys[j] = pre;
+    }
+    __syncthreads();
+    for (int c = t; c <= kYCells; c += 1024) {
+        int64_t lo = 0, hi = nsplit;  // splitters with output cell below c
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int)ycell_of(ys[mid]) < c) lo = mid + 1;
+            else hi = mid;
+        }
+        ylut[c] = (uint16_t)lo;
+    }
+}
+
+// The network's output for m inputs (the evaluation the classifier uses).
+__global__ void mlp_predict_kernel(const MlpTables *T, const float *x, int64_t m, float *y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) y[i] = mlp_eval(*T, x[i]);
 }
 
 __global__ void mlp_grad_reduce_kernel(const float *part, int G, int64_t m, float *grad, float *loss) {
@@ -312,18 +532,36 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     mlp_prepare_kernel<DT><<<1, 256, 0, c.stream>>>(b, c.ly.lsd_table, npos, p.sample_size, p.n, c.ly.mlp_norm,
                                                     c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts);
     mlp_init_kernel<<<1, 256, 0, c.stream>>>(c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts, c.ly.mlp_params);
+    // full-batch Adam on every parameter: the partial gradients of the
+    // current parameters, then the step (kMlpSteps steps, one more
+    // evaluation to keep the best)
     const int64_t max_pts = std::min<int64_t>(p.sample_size, kMlpTrainPoints);
-    const int fgrid = (int)std::max<int64_t>(1, (max_pts + kMlpThreads - 1) / kMlpThreads);
-    mlp_features_kernel<<<fgrid, kMlpThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_x, c.ly.mlp_npts, c.ly.mlp_part);
-    mlp_head_kernel<<<1, kMlpHeadThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_part, c.ly.mlp_y, c.ly.mlp_npts,
-                                                         kMlpSteps, kMlpLr, c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr,
-                                                         c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr);
+    const int G = (int)std::max<int64_t>(1, (max_pts + kMlpThreads - 1) / kMlpThreads);
+    MlpOpt *opt = reinterpret_cast<MlpOpt *>(c.ly.mlp_opt);
+    for (int step = 0; step <= kMlpSteps; ++step) {
+        mlp_step_grad_kernel<<<G, kMlpThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_x, c.ly.mlp_y,
+                                                              c.ly.mlp_npts, c.ly.mlp_part);
+        mlp_adam_kernel<<<1, 1024, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_part, G, c.ly.mlp_npts, opt, step,
+                                                  step == kMlpSteps, c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr,
+                                                  c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr);
+    }
+    // the trained network in its evaluation form, and the index over the
+    // splitters' outputs
+    mlp_tables_kernel<<<1, 64, 0, c.stream>>>(c.ly.mlp_params, opt->start, c.ly.mlp_norm, c.ly.mlp_tables);
+    const int64_t nsplit = p.P - 1;
+    if (nsplit > 0)
+        mlp_ysplit_kernel<DT><<<(unsigned)((nsplit + 255) / 256), 256, 0, c.stream>>>(
+            c.ly.mlp_tables, (const K *)c.ly.vphi, nsplit, c.ly.mlp_ysplit);
+    mlp_ylut_kernel<<<1, 1024, 0, c.stream>>>(c.ly.mlp_ysplit, nsplit, c.ly.ylut);
     cudaError_t e = cudaGetLastError();
     if (c.dbg.mlp_params)
         e = cudaMemcpyAsync(c.dbg.mlp_params, c.ly.mlp_params, sizeof(float) * kParams, cudaMemcpyDeviceToDevice,
                             c.stream);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+int mlp_train_kernels() { return 2 + 2 * (kMlpSteps + 1) + 3; }
+size_t mlp_opt_bytes() { return sizeof(MlpOpt); }
 
 cudaError_t launch_mlp_train(const Ctx &c) {
     switch (c.pl.dtype) {
@@ -341,7 +579,7 @@ using namespace bsps;
 extern "C" int bsps_mlp_workspace_size(int64_t m, size_t *bytes) {
     if (!bytes || m < 0) return BSPS_ERR_INVALID_ARG;
     const int64_t G = (m + kMlpThreads - 1) / kMlpThreads;
-    *bytes = (size_t)std::max<int64_t>(G, 1) * (kParams + 1) * sizeof(float) + 256;
+    *bytes = std::max((size_t)std::max<int64_t>(G, 1) * (kParams + 1) * sizeof(float), sizeof(MlpTables)) + 256;
     return BSPS_OK;
 }
 
@@ -355,5 +593,16 @@ extern "C" int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const
     cudaStream_t s = (cudaStream_t)stream;
     mlp_grad_kernel<<<G, kMlpThreads, 0, s>>>(d_params, d_x, d_y, m, (float *)d_ws);
     mlp_grad_reduce_kernel<<<(kParams + 1 + 255) / 256, 256, 0, s>>>((const float *)d_ws, G, m, d_grad, d_loss);
+    return cudaGetLastError() == cudaSuccess ? BSPS_OK : BSPS_ERR_CUDA;
+}
+
+extern "C" int bsps_mlp_predict(const float *d_params, const float *d_x, int64_t m, float *d_y, void *d_ws,
+                                size_t ws_bytes, void *stream) {
+    if (m < 0 || !d_params || (m > 0 && (!d_x || !d_y))) return BSPS_ERR_INVALID_ARG;
+    if (!d_ws || ws_bytes < sizeof(MlpTables) || ((uintptr_t)d_ws & 15) != 0) return BSPS_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpTables *T = (MlpTables *)d_ws;
+    mlp_tables_kernel<<<1, 64, 0, s>>>(d_params, nullptr, nullptr, T);
+    if (m > 0) mlp_predict_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(T, d_x, m, d_y);
     return cudaGetLastError() == cudaSuccess ? BSPS_OK : BSPS_ERR_CUDA;
 }

@@ -3,9 +3,11 @@
 // A 1 -> 32 -> 32 -> 1 ReLU network, FP32, estimates the cumulative
 // distribution of the keys; it is trained on the sample the method draws
 // anyway (Fig. 1 step 4 / Fig. 3 step 4), against the empirical CDF of the
-// sorted sample.  A key's predicted sub-bucket floor(P * y) is then corrected
-// by a bounded search against the true splitters, so the bucket is exactly
-// #{i : S_i <= key} (Fig. 2 step 9) whatever the network predicts.
+// sorted sample, and is evaluated through its piecewise-linear form.  Its
+// output indexes a table of the splitters' own outputs,
+// and a search against the true splitters in the indexed range, checked at
+// the range's ends, makes every bucket exactly #{i : S_i <= key} (Fig. 2
+// step 9) whatever the network predicts.
 //
 // Parameter vector (1153 floats): W1[32] b1[32] W2[32][32] (row i = unit i of
 // layer 2) b2[32] w3[32] b3.
@@ -49,27 +51,53 @@ template <int DT> __host__ __device__ __forceinline__ double key_value(typename 
     }
 }
 
-// Forward pass for one input; weights in shared (or global) memory.
-__device__ __forceinline__ float mlp_forward(const float *__restrict__ w, float x) {
-    float h1[kH];
-#pragma unroll
-    for (int j = 0; j < kH; ++j) h1[j] = fmaxf(fmaf(w[kW1 + j], x, w[kB1 + j]), 0.0f);
-    float y = w[kB3];
-#pragma unroll 4
-    for (int i = 0; i < kH; ++i) {
-        const float4 *row = reinterpret_cast<const float4 *>(w + kW2 + i * kH);
-        float z = w[kB2 + i];
-#pragma unroll
-        for (int q = 0; q < kH / 4; ++q) {
-            const float4 r = row[q];
-            z = fmaf(r.x, h1[4 * q], z);
-            z = fmaf(r.y, h1[4 * q + 1], z);
-            z = fmaf(r.z, h1[4 * q + 2], z);
-            z = fmaf(r.w, h1[4 * q + 3], z);
-        }
-        y = fmaf(w[kW3 + i], fmaxf(z, 0.0f), y);
+// ---------------------------------------------------------------------------
+// Evaluation form of the trained network.  The network is a continuous
+// piecewise-linear function of its input x: layer 1's units switch at their
+// knots t_j = -b1_j / w1_j, and between two consecutive knots layer 2's
+// pre-activations are affine in x, so each of its units switches at most once
+// more there.  Cut at all these points, the function is linear on each piece:
+//     y(x) = y_p + s_p (x - x_p)     (x_p: the piece's anchor, y_p = y(x_p)),
+// with y_p and s_p computed in double from the trained weights.  A key finds
+// its piece by a fixed-depth search over the sorted cut points and is
+// evaluated by one fused multiply-add: the network's own function, with an
+// error set by x's rounding alone.  When every slope is >= 0 the value is
+// also clamped to the piece's two end values, stored once (shared by
+// neighbouring pieces) and made nondecreasing, so that the evaluated function
+// is then exactly nondecreasing in x.
+// ---------------------------------------------------------------------------
+constexpr int kYCellBits = 14;                 // cells of the index over the network's output
+constexpr int kYCells = 1 << kYCellBits;
+constexpr int kMlpPiecesAll = (kH + 1) * (kH + 1);  // at most 33 layer-1 intervals x 33 layer-2 pieces
+constexpr int kMlpPieces = 256;                // pieces kept (else the spline start, at most 33, is used)
+constexpr int kMlpCutsPad = kMlpPieces;        // cut points, padded to a power of two with +inf
+struct MlpTables {
+    float cut[kMlpCutsPad];    // ascending left ends of pieces 1 .. np-1, then +inf
+    float4 piece[kMlpPieces];  // (x_p, y_p, s_p, y_{p+1}) of piece p = [cut[p-1], cut[p])
+    int32_t npieces;
+    int32_t npad;              // power of two > npieces - 1 (entries searched)
+    int32_t monotone;          // every slope >= 0: the evaluation is nondecreasing
+    int32_t pad_;
+    MlpNorm norm;
+};
+
+__device__ __forceinline__ float mlp_eval(const MlpTables &T, float x) {
+    // p = number of cut points <= x (a fixed-depth search)
+    int p = 0;
+    for (int st = T.npad >> 1; st >= 1; st >>= 1) p += T.cut[p + st - 1] <= x ? st : 0;
+    const float4 pc = T.piece[p];
+    float y = fmaf(pc.z, x - pc.x, pc.y);
+    if (T.monotone) {  // clamped to the piece's end values
+        y = fminf(y, pc.w);
+        if (p > 0) y = fmaxf(y, pc.y);  // piece 0 extends to -inf; its anchor is its right end
     }
     return y;
+}
+
+// Cell of the index over the network's output y (an estimate of the key's
+// rank fraction): floor(y * kYCells) clamped to [0, kYCells - 1]; NaN -> 0.
+__device__ __forceinline__ uint32_t ycell_of(float y) {
+    return (uint32_t)fminf(fmaxf(y * (float)kYCells, 0.0f), (float)(kYCells - 1));
 }
 
 // Exact bucket #{j : S_j <= e} from a predicted one: check the guess against
@@ -123,14 +151,53 @@ __device__ __forceinline__ uint32_t correct_bucket(uint32_t guess, K phi, uint32
     return lo;
 }
 
+// Learned classification (Fig. 2 step 9 with a learned first stage): the
+// network's output picks a cell of the index ylut, whose entries count the
+// splitters whose own output lies below the cell (outputs made nondecreasing
+// by a running maximum).  When the network is nondecreasing the key's bucket
+// lies between the cell's two counts; a binary search over those splitters
+// finds it.  When the evaluation is exactly nondecreasing (every slope of
+// the network >= 0) that is the bucket; otherwise a check against the
+// splitters just outside the range makes the result exact whatever the
+// network predicts: a key outside the range (a misprediction) is found by
+// galloping from there.  `mis` is set for a misprediction; `steps` counts
+// the splitter comparisons.
 template <int DT>
-__device__ __forceinline__ uint32_t classify_learned(typename KeyTraits<DT>::T bits, uint32_t tag, const float *w,
-                                                     const MlpNorm &nm, uint32_t P, const typename KeyTraits<DT>::T *sphi,
-                                                     const uint32_t *stag, uint32_t &steps) {
-    const float y = mlp_forward(w, mlp_input<DT>(bits, nm)) * (float)P;
-    uint32_t g = 0;
-    if (y >= 1.0f) g = y >= (float)(P - 1) ? P - 1 : (uint32_t)y;  // NaN -> 0
-    return correct_bucket(g, KeyTraits<DT>::phi(bits), tag, P - 1, sphi, stag, steps);
+__device__ __forceinline__ uint32_t classify_learned(typename KeyTraits<DT>::T bits, uint32_t tag,
+                                                     const MlpTables &T, const uint16_t *ylut, uint32_t nsplit,
+                                                     const typename KeyTraits<DT>::T *sphi, const uint32_t *stag,
+                                                     uint32_t &steps, bool &mis) {
+    using K = typename KeyTraits<DT>::T;
+    const K phi = KeyTraits<DT>::phi(bits);
+    auto le = [&](uint32_t j) {
+        const K sp = sphi[j];
+        return sp < phi || (sp == phi && stag[j] <= tag);
+    };
+    const float x = mlp_input<DT>(bits, T.norm);
+    const uint32_t c = ycell_of(mlp_eval(T, x));
+    const uint32_t lo0 = ylut[c], hi0 = ylut[c + 1];
+    uint32_t lo = lo0, hi = hi0;
+    steps = 0;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        ++steps;
+        if (le(mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    // A nondecreasing network (and a finite x) puts the bucket inside the
+    // cell's range: a splitter of a lower cell has a lower output, hence a
+    // lower x, hence a smaller key.  Otherwise the range is checked.
+    mis = false;
+    if (T.monotone && fabsf(x) <= 3.4028234663852886e38f) return lo;
+    bool ok = true;
+    if (lo == lo0 && lo > 0) { ++steps; ok = le(lo - 1); }
+    if (ok && lo == hi0 && lo < nsplit) { ++steps; ok = !le(lo); }
+    mis = !ok;
+    if (ok) return lo;
+    uint32_t more;
+    const uint32_t b = correct_bucket(lo, phi, tag, nsplit, sphi, stag, more);
+    steps += more;
+    return b;
 }
 
 } // namespace bsps

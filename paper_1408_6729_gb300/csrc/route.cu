@@ -39,8 +39,8 @@ template <typename K> struct RouteArgs {
     uint32_t *reg_vals;
     int64_t cap;
     DevStatus *st;
-    const float *mlp_params;     // learned classifier (nullable)
-    const MlpNorm *mlp_norm;
+    const MlpTables *mlp_tables;  // learned classifier (nullable): the network's evaluation form
+    const uint16_t *ylut;         // ... and the index over its output
     int64_t stall_tile;          // test hook: tile stall_tile - 1 never publishes (0: none)
     uint32_t spin_limit;         // polls of one bounded wait
 };
@@ -66,7 +66,7 @@ template <typename K, bool LEARNED = false> struct RouteSmemLayout {
             sphi_in_smem = pass < 2;
             stag_in_smem = pass == 0;
             size_t o = (sizeof(RouteFixed<K>) + 15) & ~size_t(15);
-            mlp = o;     o += LEARNED ? sizeof(float) * (kParams + 3) + sizeof(MlpNorm) : 0;
+            mlp = o;     o += LEARNED ? sizeof(MlpTables) : 0;
             o = (o + 15) & ~size_t(15);
             lut = o;     o += sizeof(uint16_t) * (kLutCells + 1);
             o = (o + 15) & ~size_t(15);
@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     using Rank = BlockRank<TH, IT, 8>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RouteSmemLayout<K, LEARNED> L(a.P);
-    float *mw = reinterpret_cast<float *>(smem_raw + L.mlp);
-    MlpNorm *mnorm = reinterpret_cast<MlpNorm *>(mw + kParams + 3);
+    MlpTables *mt = reinterpret_cast<MlpTables *>(smem_raw + L.mlp);
     uint32_t n_mis = 0, n_steps = 0;
     RouteFixed<K> &fx = *reinterpret_cast<RouteFixed<K> *>(smem_raw);
     uint16_t *lut = reinterpret_cast<uint16_t *>(smem_raw + L.lut);
@@ -116,14 +115,18 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
     const uint32_t P = a.P, nsplit = P - 1;
 
     // splitters and radix index into shared memory (Fig. 1 step 7, "broadcast")
-    for (int i = tid; i <= kLutCells; i += TH) lut[i] = a.lut[i];
+    // (with the learned classifier: the index over the network's output)
+    static_assert(kYCells == kLutCells, "the learned index takes the radix index's slot");
+    const uint16_t *lut_src = LEARNED ? a.ylut : a.lut;
+    for (int i = tid; i <= kLutCells; i += TH) lut[i] = lut_src[i];
     if (L.sphi_in_smem)
         for (uint32_t i = tid; i < nsplit; i += TH) sphi_s[i] = a.vphi[i];
     if (L.stag_in_smem)
         for (uint32_t i = tid; i < nsplit; i += TH) stag_s[i] = a.vtag[i];
     if constexpr (LEARNED) {
-        for (int k = tid; k < kParams; k += TH) mw[k] = a.mlp_params[k];
-        if (tid == 0) *mnorm = *a.mlp_norm;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.mlp_tables);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(mt);
+        for (int k = tid; k < (int)(sizeof(MlpTables) / 4); k += TH) dst[k] = src[k];
     }
     if (tid == 0) fx.lp = *a.lutp;
     __syncthreads();
@@ -157,8 +160,10 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                 if constexpr (LEARNED) {
                     if (ok) {
                         uint32_t steps;
-                        b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), mw, *mnorm, P, sphi, stag, steps);
-                        n_mis += steps > 0;
+                        bool mis;
+                        b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), *mt, lut, nsplit, sphi, stag, steps,
+                                                 mis);
+                        n_mis += mis;
                         n_steps += steps;
                     }
                 } else {
@@ -407,8 +412,8 @@ template <int DT, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) 
     a.reg_vals = c.ly.reg_vals;
     a.cap = p.cap;
     a.st = c.ly.status;
-    a.mlp_params = c.ly.mlp_params;
-    a.mlp_norm = c.ly.mlp_norm;
+    a.mlp_tables = c.ly.mlp_tables;
+    a.ylut = c.ly.ylut;
     a.stall_tile = c.dbg.stall_tile;
     a.spin_limit = c.dbg.wait_polls ? c.dbg.wait_polls : kSpinLimit;
     const size_t smem = RouteSmemLayout<K, LEARNED>((uint32_t)p.P).total;

@@ -17,9 +17,13 @@ namespace bsps {
 
 constexpr int kRkThreads = 1024;
 constexpr int kEarly = 4;  // buckets per thread reserved before the grouping
-constexpr size_t kRkSmemBudget = 200 * 1024;  // splitters in shared memory up to this size
-// keys per thread (fewer with the network's registers in use)
-template <typename K, bool LEARNED = false> constexpr int rk_items() { return sizeof(K) == 8 || LEARNED ? 8 : 16; }
+constexpr size_t kRkSmemBudget = 227 * 1024;  // splitters in shared memory up to this size
+// keys per thread (fewer with the network's registers in use; 8-byte keys
+// with the learned classifier: six, so that 8192 sub-buckets' splitters fit
+// shared memory next to the index over the network's output)
+template <typename K, bool LEARNED = false> constexpr int rk_items() {
+    return sizeof(K) == 8 ? (LEARNED ? 6 : 8) : (LEARNED ? 8 : 16);
+}
 template <typename K, bool LEARNED = false> constexpr int rk_chunk() { return kRkThreads * rk_items<K, LEARNED>(); }
 
 template <typename K> struct RouteKeysArgs {
@@ -35,13 +39,14 @@ template <typename K> struct RouteKeysArgs {
     K *reg_keys;
     int64_t cap;
     DevStatus *st;
-    const float *mlp_params;     // learned classifier (nullable)
-    const MlpNorm *mlp_norm;
+    const MlpTables *mlp_tables;  // learned classifier (nullable): the network's evaluation form
+    const uint16_t *ylut;         // ... and the index over its output
 };
 
-// Shared memory: the radix index, the splitters' phi (global memory, L1-cached,
-// when they do not fit), per-bucket counts and write offsets, and the chunk
-// grouped by bucket.
+// Shared memory: the radix index (with the learned classifier: the index over
+// the network's output, in the same slot, and the network's tables), the
+// splitters' phi (global memory, L1-cached, when they do not fit), per-bucket
+// counts and write offsets, and the chunk grouped by bucket.
 template <typename K, bool LEARNED> struct RouteKeysLayout {
     size_t mlp, lut, sphi, cnt, dlt, stage_k, stage_b, total;
     bool sphi_in_smem;
@@ -49,7 +54,7 @@ template <typename K, bool LEARNED> struct RouteKeysLayout {
         for (int pass = 0; pass < 2; ++pass) {
             sphi_in_smem = pass == 0;
             size_t o = 64;  // LutParams
-            mlp = o;     o += LEARNED ? sizeof(float) * (kParams + 3) + sizeof(MlpNorm) : 0;
+            mlp = o;     o += LEARNED ? sizeof(MlpTables) : 0;
             o = (o + 15) & ~size_t(15);
             lut = o;     o += sizeof(uint16_t) * (kLutCells + 2);
             o = (o + 15) & ~size_t(15);
@@ -76,8 +81,7 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RouteKeysLayout<K, LEARNED> L(a.P);
     LutParams<K> &lps = *reinterpret_cast<LutParams<K> *>(smem_raw);
-    float *mw = reinterpret_cast<float *>(smem_raw + L.mlp);
-    MlpNorm *mnorm = reinterpret_cast<MlpNorm *>(mw + kParams + 3);
+    MlpTables *mt = reinterpret_cast<MlpTables *>(smem_raw + L.mlp);
     uint16_t *lut = reinterpret_cast<uint16_t *>(smem_raw + L.lut);
     K *sphi_s = reinterpret_cast<K *>(smem_raw + L.sphi);
     const K *sphi = L.sphi_in_smem ? sphi_s : a.vphi;
@@ -89,13 +93,16 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t P = a.P;
-    for (int i = tid; i <= kLutCells; i += T) lut[i] = a.lut[i];
+    static_assert(kYCells == kLutCells, "the learned index takes the radix index's slot");
+    const uint16_t *lut_src = LEARNED ? a.ylut : a.lut;
+    for (int i = tid; i <= kLutCells; i += T) lut[i] = lut_src[i];
     if (L.sphi_in_smem)
         for (uint32_t i = tid; i + 1 < P; i += T) sphi_s[i] = a.vphi[i];
     for (uint32_t b = tid; b < P; b += T) cnt[b] = 0;
     if constexpr (LEARNED) {
-        for (int q = tid; q < kParams; q += T) mw[q] = a.mlp_params[q];
-        if (tid == 0) *mnorm = *a.mlp_norm;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.mlp_tables);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(mt);
+        for (int q = tid; q < (int)(sizeof(MlpTables) / 4); q += T) dst[q] = src[q];
     }
     if (tid == 0) lps = *a.lutp;
     __syncthreads();
@@ -148,8 +155,9 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
                 const uint32_t g = (uint32_t)(e0 + q);  // tag: input position
                 if constexpr (LEARNED) {
                     uint32_t steps;
-                    b = classify_learned<DT>(raw, g, mw, *mnorm, P, sphi, a.vtag, steps);
-                    n_mis += steps > 0;
+                    bool mis;
+                    b = classify_learned<DT>(raw, g, *mt, lut, P - 1, sphi, a.vtag, steps, mis);
+                    n_mis += mis;
                     n_steps += steps;
                 } else {
                     b = classify_key(ph, g, lp, lut, sphi, a.vtag);
@@ -298,8 +306,8 @@ template <int DT, bool LEARNED> static cudaError_t launch_t(const Ctx &c) {
     a.reg_keys = (K *)c.ly.reg_keys;
     a.cap = p.cap;
     a.st = c.ly.status;
-    a.mlp_params = c.ly.mlp_params;
-    a.mlp_norm = c.ly.mlp_norm;
+    a.mlp_tables = c.ly.mlp_tables;
+    a.ylut = c.ly.ylut;
     if (a.chunks == 0) return cudaSuccess;
     const size_t smem = RouteKeysLayout<K, LEARNED>((uint32_t)p.P).total;
     auto kern = route_keys_kernel<DT, LEARNED>;
@@ -332,6 +340,13 @@ size_t route_keys_smem_bytes(const Plan &pl) {
     const bool l = pl.classify == BSPS_LEARNED;
     if (pl.key_bytes == 8) return l ? RouteKeysLayout<uint64_t, true>(P).total : RouteKeysLayout<uint64_t, false>(P).total;
     return l ? RouteKeysLayout<uint32_t, true>(P).total : RouteKeysLayout<uint32_t, false>(P).total;
+}
+
+bool route_keys_splitters_in_smem(const Plan &pl) {
+    const uint32_t P = (uint32_t)pl.P;
+    const bool l = pl.classify == BSPS_LEARNED;
+    if (pl.key_bytes == 8) return l ? RouteKeysLayout<uint64_t, true>(P).sphi_in_smem : RouteKeysLayout<uint64_t, false>(P).sphi_in_smem;
+    return l ? RouteKeysLayout<uint32_t, true>(P).sphi_in_smem : RouteKeysLayout<uint32_t, false>(P).sphi_in_smem;
 }
 
 } // namespace bsps

@@ -918,17 +918,21 @@ __global__ void splitter_records_kernel(const K *vphi, const uint32_t *vtag, int
 }
 
 // Per-key buckets of the keys (diagnostics).  With the learned classifier
-// every key goes through the same classify_learned (prediction + correction)
-// the routing kernel uses, so its result can be compared key by key.
+// every key goes through the same classify_learned (network, index over its
+// output, search and check) the routing kernels use, so its result can be
+// compared key by key.
 template <int DT, bool LEARNED>
 __global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits<DT>::T *keys, int64_t n, int64_t B,
                                  const typename KeyTraits<DT>::T *vphi, const uint32_t *vtag,
                                  const uint16_t *lut,
-                                 const LutParams<typename KeyTraits<DT>::T> *lutp, const float *mlp_params,
-                                 const MlpNorm *mlp_norm, int64_t P, int32_t *out) {
-    __shared__ __align__(16) float w[LEARNED ? kParams + 3 : 1];
+                                 const LutParams<typename KeyTraits<DT>::T> *lutp, const MlpTables *mlp_tables,
+                                 const uint16_t *ylut, int64_t P, int32_t *out) {
+    __shared__ __align__(16) unsigned char mt_raw[LEARNED ? sizeof(MlpTables) : 16];
+    const MlpTables *mt = reinterpret_cast<const MlpTables *>(mt_raw);
     if constexpr (LEARNED) {
-        for (int q = threadIdx.x; q < kParams; q += blockDim.x) w[q] = mlp_params[q];
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(mlp_tables);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(mt_raw);
+        for (int q = threadIdx.x; q < (int)(sizeof(MlpTables) / 4); q += blockDim.x) dst[q] = src[q];
         __syncthreads();
     }
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -936,7 +940,8 @@ __global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits
     uint32_t v;
     if constexpr (LEARNED) {
         uint32_t steps;
-        v = classify_learned<DT>(keys[g], (uint32_t)g, w, *mlp_norm, (uint32_t)P, vphi, vtag, steps);
+        bool mis;
+        v = classify_learned<DT>(keys[g], (uint32_t)g, *mt, ylut, (uint32_t)(P - 1), vphi, vtag, steps, mis);
     } else {
         const LutParams<typename KeyTraits<DT>::T> lp = *lutp;
         v = classify_key(KeyTraits<DT>::phi(keys[g]), (uint32_t)g, lp, lut, vphi, vtag);
@@ -1162,7 +1167,7 @@ template <int DT> static cudaError_t launch_debug_t(const Ctx &c) {
         auto kern = p.classify == BSPS_LEARNED ? bucket_of_kernel<DT, true> : bucket_of_kernel<DT, false>;
         kern<<<(unsigned)((p.n + 255) / 256), 256, 0, c.stream>>>(
             (const K *)c.keys_in, p.n, p.B, (const K *)c.ly.vphi, c.ly.vtag, c.ly.lut,
-            (const LutParams<K> *)c.ly.lutp, c.ly.mlp_params, c.ly.mlp_norm, p.P, c.dbg.bucket_of);
+            (const LutParams<K> *)c.ly.lutp, c.ly.mlp_tables, c.ly.ylut, p.P, c.dbg.bucket_of);
     }
     if (c.dbg.pad_sizes) {
         cudaError_t e = cudaMemsetAsync(c.dbg.pad_sizes, 0, sizeof(int64_t) * p.p, c.stream);
