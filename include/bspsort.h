@@ -216,10 +216,11 @@ int bsps_read_stats(const void *d_ws, bsps_stats *stats, void *stream);
  * Learned classifier (params.classify = BSPS_LEARNED; not in the paper).  A
  * 1->32->32->1 ReLU network (FP32) fits the empirical CDF of the sorted sample
  * the method draws (Fig. 3 step 4 / Fig. 1 step 4): it starts as the
- * piecewise-linear interpolant of up to 4096 sample points at 33 knots and is
- * then trained on the GPU by full-batch Adam steps on all of its parameters
- * (the forward and backward pass behind bsps_mlp_loss_grad), keeping the
- * parameters of the lowest loss.  It is evaluated exactly in its
+ * piecewise-linear interpolant of up to 4096 sample points at 33 knots (each
+ * unit's three weights rescaled to equal size, the same function) and is then
+ * trained on the GPU by full-batch gradient descent with backtracking on all
+ * of its parameters (the forward and backward pass behind
+ * bsps_mlp_loss_grad), so that its loss never rises.  It is evaluated exactly in its
  * piecewise-affine form: between two consecutive knots of layer 1, layer 2's
  * pre-activations are an affine function of the input.  Its output indexes a
  * table counting, per output cell, the splitters whose own output lies below

@@ -12,8 +12,11 @@ against the true splitters corrects every prediction, so buckets are exactly
 Network: x -> h1 = relu(W1 x + b1) (32) -> h2 = relu(W2 h1 + b2) (32)
 -> y = w3 . h2 + b3.  Loss: mean squared error against the empirical CDF of
 the sorted sample, y_i = (i + 1/2) / S.  Training starts from the
-piecewise-linear interpolant of the training points (spline_start) and takes
-full-batch gradient steps on the output layer (head_step).  Parameters are packed in one vector
+piecewise-linear interpolant of the training points (spline_start), its
+units rescaled so that each carries its weight equally over its three
+weights (the same function, better conditioned), and takes full-batch
+gradient-descent steps on all parameters with backtracking (descent).
+Parameters are packed in one vector
 in the order W1 (32), b1 (32), W2 (32x32, row-major, W2[i, j] multiplies
 h1[j] into unit i), b2 (32), w3 (32), b3 (1): 1153 values.
 """
@@ -69,14 +72,17 @@ def loss_and_grad(theta, x, target):
 
 
 KNOTS = H + 1      # knots of the spline start
-HEAD = slice(2 * H + H * H + H, N_PARAMS)   # w3 and b3: the trained parameters
 
 
 def spline_start(x, y):
     """Parameters of the piecewise-linear interpolant of the points (x, y)
     (x ascending) at KNOTS knots of evenly spaced index j*(M-1)//H, equal x
-    merged (the later y kept): unit j of layer 1 is relu(x - knot_j), layer 2
-    is the identity, the output weights are the slope changes."""
+    merged (the later y kept): unit j of layer 1 is relu(x - knot_j), unit j of
+    layer 2 passes it on, the output weights are the slope changes.  Each
+    unit j is then rescaled: with a = |w3_j|^(1/3), its layer-1 weights and
+    its layer-2 weight are multiplied by a and its output weight divided by
+    a^2 -- relu(a z) = a relu(z) for a > 0, so the function is unchanged and
+    the three weights carry |w3_j| equally."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     M = x.shape[0]
@@ -96,14 +102,37 @@ def spline_start(x, y):
     b2 = np.zeros(H)
     w3 = np.array([(slope[0] if j == 0 else slope[j] - slope[j - 1]) if j < segs else 0.0 for j in range(H)])
     b3 = ky[0] if kx else 0.0
+    for j in range(segs):
+        if w3[j] != 0.0:
+            a = abs(w3[j]) ** (1.0 / 3.0)
+            W1[j] *= a
+            b1[j] *= a
+            W2[j, j] *= a
+            w3[j] /= a * a
     return np.concatenate([W1, b1, W2.ravel(), b2, w3, [b3]]), np.array(kx), np.array(ky)
 
 
-def head_step(theta, grad, lr):
-    """One gradient-descent step on the output layer (w3, b3) only."""
-    theta = np.array(theta, dtype=np.float64)
-    theta[HEAD] -= lr * np.asarray(grad, dtype=np.float64)[HEAD]
-    return theta
+def descent(theta, x, y, steps, first=0.1, grow=1.5, shrink=0.25):
+    """Full-batch gradient descent on all parameters with backtracking: from
+    the best parameters so far, a step of size eta along the negative
+    gradient (first eta = first * loss / |grad|^2, so that the linear model
+    predicts a drop of that fraction of the loss); a step that lowers the
+    loss is kept and eta grows, else it is dropped and eta shrinks.  Returns
+    the best parameters and the loss after each step (never increasing)."""
+    best = np.array(theta, dtype=np.float64)
+    lb, gb = loss_and_grad(best, x, y)
+    eta = first * lb / max(float(np.dot(gb, gb)), 1e-300)
+    losses = [lb]
+    for _ in range(steps):
+        cand = best - eta * gb
+        l, g = loss_and_grad(cand, x, y)
+        if l < lb:
+            best, lb, gb = cand, l, g
+            eta *= grow
+        else:
+            eta *= shrink
+        losses.append(lb)
+    return best, losses
 
 
 def predict_bucket(theta, x, P):

@@ -1,6 +1,7 @@
 // mlp.cu -- the learned bucket classifier on the GPU: the training set from
-// the sorted sample, the spline start, full-batch Adam steps on every
-// parameter (the forward and backward pass of mlp_cta_grad, checked against
+// the sorted sample, the spline start, full-batch gradient descent with
+// backtracking on every parameter (the forward and backward pass of
+// mlp_cta_grad, checked against
 // the CPU oracle through bsps_mlp_loss_grad), the evaluation tables of the
 // trained network, and the index over the splitters' outputs.
 #include <algorithm>
@@ -11,14 +12,14 @@ namespace bsps {
 
 constexpr int kMlpThreads = 128;       // one training point per thread per step
 constexpr int kMlpMaxPoints = kMlpPointsMax;
-// Full-batch Adam on all 1153 parameters from the spline start.  Each
-// parameter's step is relative to its own scale: a layer-1 bias moves its
-// knot, so its scale is the gap to the nearest other knot (knots inside a
-// narrow mode of the keys are 1e-5 apart, output slopes reach thousands);
-// the other parameters scale with their magnitude.  The parameters of the
-// lowest loss seen are kept.
+// Full-batch gradient descent on all 1153 parameters from the (balanced)
+// spline start, with backtracking: each step goes from the best parameters
+// so far along their negative gradient; a step that lowers the loss is kept
+// and the step size grows, else it is dropped and the step size shrinks.
+// The first step size is a tenth of loss / |gradient|^2 (the linear model's
+// step to a tenth of the loss).
 constexpr int kMlpSteps = 8;
-constexpr float kMlpLr = 5e-4f;        // step, relative to the parameter's scale
+constexpr float kMlpFirst = 0.1f, kMlpGrow = 1.5f, kMlpShrink = 0.25f;
 constexpr int kMlpTrainPoints = 4096;  // training points drawn from the sorted sample
 
 // Per-CTA gradient of the mean squared error over the CTA's points
@@ -142,96 +143,85 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_grad_kernel(const float 
     if (threadIdx.x == 0) pp[kParams] = lp;
 }
 
-// Adam state: first and second moments, the best parameters and their loss.
+// Descent state: the best parameters, their loss and gradient, the step size.
 struct MlpOpt {
-    float m[kParams], v[kParams], best[kParams], scale[kParams], start[kParams];
-    float best_loss;
-    float first_loss;
+    float best[kParams], grad[kParams], start[kParams];
+    float best_loss, eta;
 };
 
-// Sums the G partial gradients and losses of the current parameters, keeps
-// them as the best if their loss is the lowest so far, and (unless `last`)
-// takes one Adam step; after the last evaluation the best parameters are
-// written back.
-__global__ void __launch_bounds__(1024) mlp_adam_kernel(float *params, const float *part, int G,
-                                                        const int64_t *npts, MlpOpt *opt, int step, int last,
-                                                        float *loss_first, float *loss_last) {
-    __shared__ float s_loss;
-    const int t = threadIdx.x;
+// Sums the G partial gradients and losses of the current parameters; keeps
+// them as the best if their loss is the lowest so far (the step size grows)
+// or drops them (it shrinks); then, unless `last`, sets the parameters to the
+// next trial, best - eta * grad(best).  After the last evaluation the best
+// parameters are written back.
+__global__ void __launch_bounds__(1024) mlp_descent_kernel(float *params, const float *part, int G,
+                                                           const int64_t *npts, MlpOpt *opt, int step, int last,
+                                                           float *loss_first, float *loss_last) {
+    __shared__ float s_loss, s_red[32];
+    __shared__ int s_keep;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t m = *npts;
     if (m == 0) return;
     if (t == 0) {
         float l = 0.0f;
         for (int c = 0; c < G; ++c) l += part[(int64_t)c * (kParams + 1) + kParams];
         s_loss = l / (float)m;
+        s_keep = step == 0 || s_loss < opt->best_loss;
     }
     __syncthreads();
-    const float loss = s_loss;
-    const bool better = step == 0 || loss < opt->best_loss;
-    if (step == 0) {  // step scales of the parameters, from the start (kept too)
-        for (int k = t; k < kParams; k += 1024) {
-            opt->scale[k] = fmaxf(fabsf(params[k]), 1e-3f);
-            opt->start[k] = params[k];
-        }
-        __syncthreads();
-        if (t < kH) {
-            const float w = params[kW1 + t];
-            if (w != 0.0f) {
-                const float tj = -params[kB1 + t] / w;
-                float gap = 1.0f;
-                for (int j = 0; j < kH; ++j) {
-                    const float wj = params[kW1 + j];
-                    if (j != t && wj != 0.0f) gap = fminf(gap, fabsf(-params[kB1 + j] / wj - tj));
-                }
-                opt->scale[kB1 + t] = fmaxf(gap * fabsf(w), 1e-7f);
-            }
-        }
-        __syncthreads();
-    }
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-12f;
-    const float c1 = 1.0f - powf(b1, (float)(step + 1)), c2 = 1.0f - powf(b2, (float)(step + 1));
+    const bool keep = s_keep;
+    float g2 = 0.0f;
     for (int k = t; k < kParams; k += 1024) {
-        const float p = params[k];
-        if (better) opt->best[k] = p;
-        if (last) continue;
-        float g = 0.0f;
-        for (int c = 0; c < G; ++c) g += part[(int64_t)c * (kParams + 1) + k];
-        const float mk = step == 0 ? (1.0f - b1) * g : b1 * opt->m[k] + (1.0f - b1) * g;
-        const float vk = step == 0 ? (1.0f - b2) * g * g : b2 * opt->v[k] + (1.0f - b2) * g * g;
-        opt->m[k] = mk;
-        opt->v[k] = vk;
-        const float upd = (mk / c1) / (sqrtf(vk / c2) + eps);
-        params[k] = p - kMlpLr * opt->scale[k] * upd;
+        if (step == 0) opt->start[k] = params[k];
+        if (keep) {
+            float g = 0.0f;
+            for (int c = 0; c < G; ++c) g += part[(int64_t)c * (kParams + 1) + k];
+            opt->best[k] = params[k];
+            opt->grad[k] = g;
+            g2 = fmaf(g, g, g2);
+        }
     }
+    // |grad|^2 for the first step size
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+    if (lane == 0) s_red[warp] = g2;
     __syncthreads();
     if (t == 0) {
-        if (better) opt->best_loss = loss;
         if (step == 0) {
-            opt->first_loss = loss;
-            if (loss_first) *loss_first = loss;
+            float tot = 0.0f;
+            for (int w = 0; w < 32; ++w) tot += s_red[w];
+            opt->eta = tot > 0.0f ? kMlpFirst * s_loss / tot : 0.0f;
+            if (loss_first) *loss_first = s_loss;
+        } else {
+            opt->eta *= keep ? kMlpGrow : kMlpShrink;
         }
+        if (keep) opt->best_loss = s_loss;
+        if (last && loss_last) *loss_last = opt->best_loss;
     }
-    if (last) {
-        __syncthreads();
-        for (int k = t; k < kParams; k += 1024) params[k] = opt->best[k];
-        if (t == 0 && loss_last) *loss_last = opt->best_loss;
-    }
+    __syncthreads();
+    const float eta = opt->eta;
+    for (int k = t; k < kParams; k += 1024)
+        params[k] = last ? opt->best[k] : opt->best[k] - eta * opt->grad[k];
 }
 
 // The piecewise-linear form of the network `params` (see MlpTables), in
-// double.  Thread k < 33 takes layer 1's interval k (between its sorted knots
-// k-1 and k): it forms layer 2's affine pre-activations there, cuts the
-// interval where any of them crosses zero, and gives every piece its anchor,
-// value and slope; the pieces of all intervals are then written in order.
-// A network of more than kMlpPieces pieces is replaced by `fallback` (the
-// spline start, at most 33 pieces), when given.
-__global__ void __launch_bounds__(64) mlp_tables_kernel(const float *params_in, const float *fallback,
-                                                        const MlpNorm *norm, MlpTables *T) {
+// double.  Warp k takes layer 1's interval k (between its sorted knots k-1
+// and k), lane i layer 2's unit i: the lane forms the unit's affine
+// pre-activation there and its zero crossing; the crossings inside the
+// interval cut it into pieces, and for every piece the warp sums the active
+// units' slopes and values at the piece's anchor.  The pieces of all
+// intervals are then written in order.  A network of more than kMlpPieces
+// pieces is replaced by `fallback` (the spline start, at most 33 pieces),
+// when given.
+constexpr int kTablesThreads = 1024;
+__global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const float *params_in, const float *fallback,
+                                                                    const MlpNorm *norm, MlpTables *T) {
     __shared__ double knots[kH];
+    __shared__ double cutd[kH + 1][kH + 1];
     __shared__ int nk;
     __shared__ float s_x[kMlpPiecesAll], s_y[kMlpPiecesAll], s_s[kMlpPiecesAll];
     __shared__ int s_n[kH + 1], s_off[kH + 2];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const double INF = __longlong_as_double(0x7ff0000000000000ll);
     const float *params = params_in;
   again:
@@ -250,59 +240,61 @@ __global__ void __launch_bounds__(64) mlp_tables_kernel(const float *params_in, 
     }
     __syncthreads();
     const int c = nk;
-    if (t <= c) {
-        const int k = t;
+    const double w3 = params[kW3 + lane];
+    for (int k = warp; k <= c; k += kTablesThreads / 32) {
         const double lo = k == 0 ? -INF : knots[k - 1], hi = k == c ? INF : knots[k];
         // a point inside the interval decides which layer-1 units are on
         double xm = 0.0;
         if (c > 0) xm = k == 0 ? knots[0] - 1.0 : (k == c ? knots[c - 1] + 1.0 : 0.5 * (lo + hi));
-        double A[kH], B[kH];
-        for (int i = 0; i < kH; ++i) {
-            double a = params[kB2 + i], b = 0.0;
-            for (int j = 0; j < kH; ++j) {
-                const double w1 = params[kW1 + j], b1 = params[kB1 + j];
-                if (w1 * xm + b1 > 0.0) {
-                    const double w2 = params[kW2 + i * kH + j];
-                    a += w2 * b1;
-                    b += w2 * w1;
-                }
+        double A = params[kB2 + lane], B = 0.0;  // unit `lane` of layer 2: A + B x here
+        for (int j = 0; j < kH; ++j) {
+            const double w1 = params[kW1 + j], b1 = params[kB1 + j];
+            if (w1 * xm + b1 > 0.0) {
+                const double w2 = params[kW2 + lane * kH + j];
+                A += w2 * b1;
+                B += w2 * w1;
             }
-            A[i] = a;
-            B[i] = b;
         }
-        // cut points inside (lo, hi): zeros of the pre-activations
-        double cuts[kH + 1];
-        int m = 0;
-        for (int i = 0; i < kH; ++i)
-            if (B[i] != 0.0) {
-                const double z = -A[i] / B[i];
-                if (z > lo && z < hi) {
-                    int q = m++;
-                    while (q > 0 && cuts[q - 1] > z) { cuts[q] = cuts[q - 1]; --q; }
-                    cuts[q] = z;
-                }
-            }
+        // its zero crossing, when inside the interval, ranked among the others
+        const double z = B != 0.0 ? -A / B : 0.0;
+        const bool in = B != 0.0 && z > lo && z < hi;
+        const uint32_t valid = __ballot_sync(0xffffffffu, in);
+        int rank = 0;
+        for (int q = 0; q < 32; ++q) {
+            const double zq = __shfl_sync(0xffffffffu, z, q);
+            rank += ((valid >> q) & 1u) && (zq < z || (zq == z && q < lane));
+        }
+        if (in) cutd[k][rank] = z;
+        __syncwarp();
+        const int m = __popc(valid);
         // piece r of the interval: [left_r, right_r)
-        const int base = k * (kH + 1);
         for (int r = 0; r <= m; ++r) {
-            const double left = r == 0 ? lo : cuts[r - 1], right = r == m ? hi : cuts[r];
+            const double left = r == 0 ? lo : cutd[k][r - 1], right = r == m ? hi : cutd[k][r];
             double mid, anchor;
             if (left == -INF && right == INF) { mid = 0.0; anchor = 0.0; }
             else if (left == -INF) { mid = right - 1.0; anchor = right; }
             else if (right == INF) { mid = left + 1.0; anchor = left; }
             else { mid = 0.5 * (left + right); anchor = left; }
-            double y = params[kB3], sl = 0.0;
-            for (int i = 0; i < kH; ++i)
-                if (A[i] + B[i] * mid > 0.0) {
-                    const double w3 = params[kW3 + i];
-                    y += w3 * (A[i] + B[i] * anchor);
-                    sl += w3 * B[i];
-                }
-            s_x[base + r] = (float)anchor;
-            s_y[base + r] = (float)y;
-            s_s[base + r] = (float)sl;
+            const bool on = A + B * mid > 0.0;
+            double y = on ? w3 * (A + B * anchor) : 0.0, sl = on ? w3 * B : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y += __shfl_xor_sync(0xffffffffu, y, o);
+                sl += __shfl_xor_sync(0xffffffffu, sl, o);
+            }
+            if (lane == 0) {
+                y += params[kB3];
+                // a finite piece over which the network falls by less than
+                // 2^-30 (far below the output's float resolution and its
+                // index cells) is taken as flat
+                if (sl < 0.0 && left != -INF && right != INF && -sl * (right - left) < 9.313225746154785e-10) sl = 0.0;
+                const int q = k * (kH + 1) + r;
+                s_x[q] = (float)anchor;
+                s_y[q] = (float)y;
+                s_s[q] = (float)sl;
+            }
         }
-        s_n[k] = m + 1;
+        if (lane == 0) s_n[k] = m + 1;
     }
     __syncthreads();
     if (t == 0) {
@@ -340,8 +332,8 @@ __global__ void __launch_bounds__(64) mlp_tables_kernel(const float *params_in, 
         T->monotone = mono ? 1 : 0;
     }
     __syncthreads();
-    if (t <= c) {
-        const int k = t, o = s_off[k];
+    for (int k = t; k <= c; k += kTablesThreads) {
+        const int o = s_off[k];
         for (int r = 0; r < s_n[k] && o + r < kMlpPieces; ++r) {
             const int q = k * (kH + 1) + r;
             // the value at the piece's right end: the next piece's anchor value
@@ -355,7 +347,7 @@ __global__ void __launch_bounds__(64) mlp_tables_kernel(const float *params_in, 
     }
     __syncthreads();
     const int np = min(s_off[c + 1], kMlpPieces);
-    for (int q = np - 1 + t; q < kMlpCutsPad; q += 64) T->cut[q] = __int_as_float(0x7f800000);
+    for (int q = np - 1 + t; q < kMlpCutsPad; q += kTablesThreads) T->cut[q] = __int_as_float(0x7f800000);
 }
 
 // The network's output for every splitter (S_{j+1} at index j).
@@ -440,8 +432,9 @@ __global__ void mlp_grad_reduce_kernel(const float *part, int G, int64_t m, floa
 // Start: the network is set to the piecewise-linear interpolant of the
 // training points at 33 knots of evenly spaced rank (equal x merged): unit j
 // of layer 1 is relu(x - knot_j), layer 2 passes its input through
-// (W2 = I, b2 = 0; relu is the identity on relu outputs), and the output
-// weights are the slope changes at the knots.  Training then refines it.
+// (W2 diagonal, b2 = 0; relu is the identity on relu outputs), and the output
+// weights are the slope changes at the knots, each unit rescaled so that its
+// three weights are equal in size.  Training then refines it.
 // ---------------------------------------------------------------------------
 template <int DT>
 __global__ void mlp_prepare_kernel(LsdBuffers<typename KeyTraits<DT>::T> b, const int32_t *table, int npos, int64_t S,
@@ -506,14 +499,20 @@ __global__ void mlp_init_kernel(const float *x, const float *y, const int64_t *n
     __syncthreads();
     const int segs = nk > 1 ? nk - 1 : 0;
     auto slope = [&](int j) { return (ky[j + 1] - ky[j]) / (kx[j + 1] - kx[j]); };
+    // unit j, rescaled by a = |w3_j|^(1/3) (relu(a z) = a relu(z)): the same
+    // function with its weight carried equally by w1_j, W2_jj and w3_j
     if (t < kH) {
         const bool on = t < segs;
-        params[kW1 + t] = on ? 1.0f : 0.0f;
-        params[kB1 + t] = on ? -kx[t] : -1.0f;  // unused units stay at zero
+        const float w3 = on ? (t == 0 ? slope(0) : slope(t) - slope(t - 1)) : 0.0f;
+        const float a = w3 != 0.0f ? cbrtf(fabsf(w3)) : 1.0f;
+        params[kW1 + t] = on ? a : 0.0f;
+        params[kB1 + t] = on ? -kx[t] * a : -1.0f;  // unused units stay at zero
         params[kB2 + t] = 0.0f;
-        params[kW3 + t] = on ? (t == 0 ? slope(0) : slope(t) - slope(t - 1)) : 0.0f;
+        params[kW3 + t] = w3 / (a * a);
+        params[kW2 + t * kH + t] = a;
     }
-    for (int k = t; k < kH * kH; k += blockDim.x) params[kW2 + k] = (k / kH == k % kH) ? 1.0f : 0.0f;
+    for (int k = t; k < kH * kH; k += blockDim.x)
+        if (k / kH != k % kH) params[kW2 + k] = 0.0f;
     if (t == 0) params[kB3] = nk > 0 ? ky[0] : 0.0f;
 }
 
@@ -532,22 +531,22 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     mlp_prepare_kernel<DT><<<1, 256, 0, c.stream>>>(b, c.ly.lsd_table, npos, p.sample_size, p.n, c.ly.mlp_norm,
                                                     c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts);
     mlp_init_kernel<<<1, 256, 0, c.stream>>>(c.ly.mlp_x, c.ly.mlp_y, c.ly.mlp_npts, c.ly.mlp_params);
-    // full-batch Adam on every parameter: the partial gradients of the
-    // current parameters, then the step (kMlpSteps steps, one more
-    // evaluation to keep the best)
+    // full-batch gradient descent on every parameter: the partial gradients
+    // of the current parameters, then the step (kMlpSteps trials after the
+    // start's evaluation)
     const int64_t max_pts = std::min<int64_t>(p.sample_size, kMlpTrainPoints);
     const int G = (int)std::max<int64_t>(1, (max_pts + kMlpThreads - 1) / kMlpThreads);
     MlpOpt *opt = reinterpret_cast<MlpOpt *>(c.ly.mlp_opt);
     for (int step = 0; step <= kMlpSteps; ++step) {
         mlp_step_grad_kernel<<<G, kMlpThreads, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_x, c.ly.mlp_y,
                                                               c.ly.mlp_npts, c.ly.mlp_part);
-        mlp_adam_kernel<<<1, 1024, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_part, G, c.ly.mlp_npts, opt, step,
+        mlp_descent_kernel<<<1, 1024, 0, c.stream>>>(c.ly.mlp_params, c.ly.mlp_part, G, c.ly.mlp_npts, opt, step,
                                                   step == kMlpSteps, c.dbg.mlp_loss ? c.dbg.mlp_loss : nullptr,
                                                   c.dbg.mlp_loss ? c.dbg.mlp_loss + 1 : nullptr);
     }
     // the trained network in its evaluation form, and the index over the
     // splitters' outputs
-    mlp_tables_kernel<<<1, 64, 0, c.stream>>>(c.ly.mlp_params, opt->start, c.ly.mlp_norm, c.ly.mlp_tables);
+    mlp_tables_kernel<<<1, kTablesThreads, 0, c.stream>>>(c.ly.mlp_params, opt->start, c.ly.mlp_norm, c.ly.mlp_tables);
     const int64_t nsplit = p.P - 1;
     if (nsplit > 0)
         mlp_ysplit_kernel<DT><<<(unsigned)((nsplit + 255) / 256), 256, 0, c.stream>>>(
@@ -602,7 +601,7 @@ extern "C" int bsps_mlp_predict(const float *d_params, const float *d_x, int64_t
     if (!d_ws || ws_bytes < sizeof(MlpTables) || ((uintptr_t)d_ws & 15) != 0) return BSPS_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
     MlpTables *T = (MlpTables *)d_ws;
-    mlp_tables_kernel<<<1, 64, 0, s>>>(d_params, nullptr, nullptr, T);
+    mlp_tables_kernel<<<1, kTablesThreads, 0, s>>>(d_params, nullptr, nullptr, T);
     if (m > 0) mlp_predict_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(T, d_x, m, d_y);
     return cudaGetLastError() == cudaSuccess ? BSPS_OK : BSPS_ERR_CUDA;
 }

@@ -61,7 +61,8 @@ template <int DT> __host__ __device__ __forceinline__ double key_value(typename 
 // with y_p and s_p computed in double from the trained weights.  A key finds
 // its piece by a fixed-depth search over the sorted cut points and is
 // evaluated by one fused multiply-add: the network's own function, with an
-// error set by x's rounding alone.  When every slope is >= 0 the value is
+// error set by x's rounding alone (a piece over which the network falls by
+// less than 2^-30 is taken as flat).  When every slope is >= 0 the value is
 // also clamped to the piece's two end values, stored once (shared by
 // neighbouring pieces) and made nondecreasing, so that the evaluated function
 // is then exactly nondecreasing in x.

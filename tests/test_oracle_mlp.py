@@ -75,30 +75,56 @@ def test_spline_start_merges_equal_x():
     assert np.allclose(f, ky)
 
 
-def test_head_steps_lower_the_loss_and_beat_a_constant():
+def test_spline_start_is_balanced():
+    """Each unit's three weights carry its output weight equally (|w1_j| =
+    |W2_jj| = |w3_j|, the cube root of the plain interpolant's slope change);
+    the function is the plain interpolant's (checked above at knots and
+    midpoints), and the knots are -b1/w1."""
+    rng = np.random.default_rng(4)
+    x = np.sort(rng.random(500))
+    y = (np.arange(500) + 0.5) / 500
+    theta, kx, ky = mlp.spline_start(x, y)
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(theta)
+    on = w3 != 0
+    assert on.sum() >= 8
+    assert np.allclose(np.abs(W1[on]), np.abs(np.diag(W2))[on])
+    assert np.allclose(np.abs(W1[on]), np.abs(w3[on]))
+    slopes = np.diff(ky) / np.diff(kx)
+    change = np.concatenate([[slopes[0]], np.diff(slopes)])
+    assert np.allclose(W1[on] * np.diag(W2)[on] * w3[on], change[on[:len(change)]])
+    assert np.allclose(-b1[on] / W1[on], kx[:on.sum()])
+
+
+def test_descent_lowers_the_loss_moves_every_layer_and_beats_a_constant():
     rng = np.random.default_rng(5)
     keys = np.sort(np.concatenate([rng.normal(0, 1, 3000), rng.normal(8, 0.3, 1000)]))
     x = (keys - keys[0]) / (keys[-1] - keys[0])
     y = (np.arange(x.size) + 0.5) / x.size
     theta, _, _ = mlp.spline_start(x, y)
-    losses = []
-    for _ in range(32):
-        loss, g = mlp.loss_and_grad(theta, x, y)
-        losses.append(loss)
-        theta = mlp.head_step(theta, g, 0.02)
-    assert all(b < a for a, b in zip(losses, losses[1:]))
+    best, losses = mlp.descent(theta, x, y, 16)
+    assert all(b <= a for a, b in zip(losses, losses[1:]))
+    assert losses[-1] < losses[0]
+    moved = best - theta
+    for part in (slice(0, 32), slice(32, 64), slice(64, 64 + 1024), slice(1088, 1120), slice(1120, 1152)):
+        assert np.abs(moved[part]).max() > 0
     P = 64
     true_b = np.minimum((y * P).astype(int), P - 1)
-    pred = mlp.predict_bucket(theta, x, P)
+    pred = mlp.predict_bucket(best, x, P)
     assert np.mean(np.abs(pred - true_b)) < np.mean(np.abs(P // 2 - true_b)) / 4
 
 
-def test_head_step_moves_only_the_output_layer():
-    theta = _theta(6)
-    g = np.ones(mlp.N_PARAMS)
-    t2 = mlp.head_step(theta, g, 0.5)
-    assert np.array_equal(t2[:mlp.HEAD.start], theta[:mlp.HEAD.start])
-    assert np.allclose(t2[mlp.HEAD], theta[mlp.HEAD] - 0.5)
+def test_descent_keeps_the_start_when_no_step_helps():
+    """At a minimum (a network that already fits exactly) every step is
+    rejected and the start comes back unchanged."""
+    x = np.linspace(0, 1, 64)
+    y = 0.25 + 0.5 * x
+    theta = np.zeros(mlp.N_PARAMS)
+    theta[0] = 1.0          # W1[0]
+    theta[64] = 1.0         # W2[0][0]
+    theta[1088 + 32] = 0.5  # w3[0]
+    theta[-1] = 0.25        # b3
+    best, losses = mlp.descent(theta, x, y, 8)
+    assert losses[-1] <= 1e-30 and np.array_equal(best, theta)
 
 
 def test_prediction_is_clamped():
