@@ -153,7 +153,16 @@ bucket_keys32_kernel(const BucketArgs<uint32_t> a) {
         return;
     }
     auto emit = [&](uint32_t pos, uint32_t key) { out_k[pos] = KeyTraits<DT>::inv(key); };
-    if (!SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit) && threadIdx.x == 0) {
+    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
+    if (threadIdx.x == 0) sm.stalled = 0;
+    __syncthreads();
+    bool done = SS::run(smem_raw, a.reg_keys + v * a.cap, cnt, lo, hi, emit, a.st);
+    __syncthreads();
+    if (sm.stalled) {  // the staged load's wait ran out: wait for the copy once more, give the sub-bucket back
+        SS::wait_staged(sm, kSpinLimit);
+        done = false;
+    }
+    if (!done && threadIdx.x == 0) {
         if (atomicExch(&a.retry_flag[v], 1u) == 0u) {
             const int slot = atomicAdd(&a.st->retry_count, 1);
             a.retry_list[slot] = (uint32_t)v;

@@ -4,8 +4,9 @@
 //
 // A cluster of CL CTAs (512 threads, two CTAs per SM) sorts one sub-bucket
 // whose keys lie in [lo, hi] (bounds from the splitters around it):
-//   1. each CTA loads its share of the region into registers (16-byte loads)
-//      and ranks every key in its split bin (the top 8 bits of key - lo) with
+//   1. each CTA loads its share of the region into shared memory by one bulk
+//      asynchronous copy, reads it into registers (16-byte shared loads) and
+//      ranks every key in its split bin (the top 8 bits of key - lo) with
 //      one shared-memory atomic; bin and rank stay packed in one register;
 //   2. the keys are grouped by split bin in a local stage;
 //   3. every CTA reads the cluster's bin counts through distributed shared
@@ -64,6 +65,8 @@ struct BucketKeys32 {
         uint32_t odelta[R];   // received bin d: output position = odelta[d] + sorted position
         K bmin[R], bmax[R];   // smallest / largest key of my share per split bin (flat-bin pass)
         uint32_t list[kListMax];  // waiting slots of the keys the count sort places by comparison
+        unsigned long long mbar;  // completion of the bulk copy of this CTA's share
+        uint32_t stalled;         // the wait for that copy ran out (set to 0 by the caller)
         uint32_t orecv[CL], ofirst[CL], olast[CL], obase[CL];
         uint32_t tmp[40];
     };
@@ -108,6 +111,60 @@ struct BucketKeys32 {
         *reinterpret_cast<uint4 *>(out + lane * 8) = oa;
         *reinterpret_cast<uint4 *>(out + lane * 8 + 4) = ob;
         return tot;
+    }
+
+    // This CTA's share of the region (n keys at src, 16-byte aligned; reading
+    // up to the next 16 bytes stays inside the region) into registers through
+    // shared memory: one thread issues a bulk asynchronous copy (the tensor
+    // memory accelerator's 1-D form) into `buf` and every thread waits on an
+    // mbarrier for its completion, then reads its keys with 16-byte shared
+    // loads.  The wait is bounded: when it runs out the status records
+    // BSPS_ERR_DEVICE_TIMEOUT and sm.stalled is set; the sort then goes on
+    // (on whatever the buffer holds, every index bounded) so that the
+    // cluster's barriers stay matched, and the caller waits once more for the
+    // copy (wait_staged) and gives the sub-bucket back.
+    __device__ static bool wait_staged(Smem &sm, uint32_t limit) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
+        uint32_t done = 0;
+        for (uint32_t polls = 0; !done && polls < limit; ++polls)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+        return done != 0;
+    }
+    __device__ static void load_staged(Smem &sm, K (&k)[ITEMS], const K *__restrict__ src, int n, K *buf,
+                                       DevStatus *st) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
+        const uint32_t bytes = (uint32_t)((n * (int)sizeof(K) + 15) & ~15);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+            if (bytes)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        (uint32_t)__cvta_generic_to_shared(buf)),
+                    "l"(src), "r"(bytes), "r"(bar)
+                    : "memory");
+        }
+        if (!__syncthreads_and(wait_staged(sm, kSpinLimit)) && threadIdx.x == 0) {
+            sm.stalled = 1;
+            atomicAdd(&st->timeouts, 1);
+            set_error(st, BSPS_ERR_DEVICE_TIMEOUT);
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS / 4; ++j) {
+            const int q = j * T + (int)threadIdx.x;
+            if (q * 4 < n) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(buf + q * 4);
+                k[j * 4 + 0] = w.x; k[j * 4 + 1] = w.y; k[j * 4 + 2] = w.z; k[j * 4 + 3] = w.w;
+            }
+        }
     }
 
     // Bin lengths (with masks: one key per mask bit plus the counted later
@@ -329,7 +386,8 @@ struct BucketKeys32 {
     // lo < hi) and calls emit(position, key) for each.  Returns false when
     // the sub-bucket goes to the stable sort, which rewrites every position.
     template <typename Emit>
-    __device__ static bool run(unsigned char *smem, const K *__restrict__ src, int64_t cnt, K lo, K hi, Emit emit) {
+    __device__ static bool run(unsigned char *smem, const K *__restrict__ src, int64_t cnt, K lo, K hi, Emit emit,
+                               DevStatus *st) {
         Smem &sm = *reinterpret_cast<Smem *>(smem);
         K *regA = reinterpret_cast<K *>(smem + kSmemHead);
         K *regB = reinterpret_cast<K *>(smem + kSmemHead + kBytesA);
@@ -339,7 +397,7 @@ struct BucketKeys32 {
         K k[ITEMS];
         if constexpr (CL == 1) {
             const int n = (int)cnt;
-            load(k, src, n);
+            load_staged(sm, k, src, n, regB, st);
             auto mine = [&](int i) { return lidx(i) < n; };
             if (!count_sort(k, mine, lo, hi - lo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp, sm.list))
                 return false;
@@ -350,7 +408,7 @@ struct BucketKeys32 {
             const int c = (int)cluster.block_rank();
             const int e0 = c * (int)share;
             const int mycnt = (int)imax64(0, imin64(share, cnt - e0));
-            load(k, src + e0, mycnt);
+            load_staged(sm, k, src + e0, mycnt, regB, st);  // (the receive buffer is free until the barrier below)
             auto mine = [&](int i) { return lidx(i) < mycnt; };
             const int bits = bit_length<K>(hi - lo);
             const int shift = bits > 8 ? bits - 8 : 0;
