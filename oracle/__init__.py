@@ -27,6 +27,8 @@ _lib = None
 
 U32, I32, F32, F64 = 0, 1, 2, 3
 REGULAR, RANDOM = 0, 1
+DUP_TAGS, DUP_OFF = 0, 1      # duplicate handling of Sec. 5.1.1 on / off
+DET_IRAN, RAN = 0, 1          # Sort_Det_BSP / Sort_IRan_BSP (Fig. 1, 3), or Sort_Ran_BSP (Fig. 2)
 
 DTYPE_CODE = {np.dtype(np.uint32): U32, np.dtype(np.int32): I32,
               np.dtype(np.float32): F32, np.dtype(np.float64): F64}
@@ -35,7 +37,7 @@ DTYPE_CODE = {np.dtype(np.uint32): U32, np.dtype(np.int32): I32,
 class Params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("runs", ctypes.c_int32), ("s", ctypes.c_int64),
                 ("sampling", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("duplicates", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -69,7 +71,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
         lib.oracle_sort.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, ctypes.POINTER(Params),
-                                    P, P, P, P, P, P, P]
+                                    P, P, P, P, P, P, P, P]
         lib.oracle_sort.restype = ctypes.c_int
         lib.oracle_plan_of.argtypes = [ctypes.c_int64, ctypes.POINTER(Params), ctypes.POINTER(Plan)]
         lib.oracle_plan_of.restype = ctypes.c_int
@@ -105,9 +107,10 @@ def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
-def make_params(p, s=0, runs=0, sampling=REGULAR, seed=0, threads=0) -> Params:
+def make_params(p, s=0, runs=0, sampling=REGULAR, seed=0, threads=0, duplicates=DUP_TAGS,
+                variant=DET_IRAN) -> Params:
     return Params(p=int(p), runs=int(runs), s=int(s), sampling=int(sampling), threads=int(threads),
-                  seed=int(seed) & (2**64 - 1))
+                  seed=int(seed) & (2**64 - 1), duplicates=int(duplicates), variant=int(variant))
 
 
 def plan(n, p, s=0, runs=0, sampling=REGULAR, seed=0) -> Plan | None:
@@ -137,15 +140,19 @@ class Result:
     splitters: np.ndarray
     bucket_of: np.ndarray | None
     plan: Plan
+    partition: np.ndarray | None = None
 
 
 def sort(keys: np.ndarray, p: int, s: int = 0, runs: int = 0, sampling: int = REGULAR,
          seed: int = 0, vals: np.ndarray | None = None, want_sample: bool = True,
-         want_bucket_of: bool = False, threads: int = 0) -> Result:
+         want_bucket_of: bool = False, threads: int = 0, duplicates: int = DUP_TAGS,
+         variant: int = DET_IRAN, want_partition: bool = False) -> Result:
     """Run the BSP simulation; raises ValueError on invalid parameters.
 
     threads > 1 runs the virtual processors of each superstep on that many host
-    threads (the result is the same)."""
+    threads (the result is the same).  duplicates = DUP_OFF drops the tags from
+    the partition's comparisons; variant = RAN runs Sort_Ran_BSP (Fig. 2).
+    want_partition returns c[k][i] (SS6) as an R x (p+1) array."""
     keys = np.ascontiguousarray(keys)
     code = DTYPE_CODE[keys.dtype]
     n = keys.shape[0]
@@ -162,10 +169,11 @@ def sort(keys: np.ndarray, p: int, s: int = 0, runs: int = 0, sampling: int = RE
     sample = np.zeros(pl.sample_size, RECORD_DTYPE) if (want_sample and n > 0) else None
     spl = np.zeros(max(pl.p - 1, 0), RECORD_DTYPE)
     bof = np.full(n, -1, np.int32) if want_bucket_of else None
-    prm = make_params(p, s, runs, sampling, seed, threads)
+    part = np.zeros((pl.R, pl.p + 1), np.int64) if (want_partition and n > 0) else None
+    prm = make_params(p, s, runs, sampling, seed, threads, duplicates, variant)
     rc = _load().oracle_sort(code, _ptr(keys), _ptr(vals), n, ctypes.byref(prm), _ptr(keys_out),
                              _ptr(vals_out), _ptr(sizes), _ptr(pads), _ptr(sample), _ptr(spl),
-                             _ptr(bof))
+                             _ptr(bof), _ptr(part))
     if rc:
         raise ValueError(f"oracle_sort failed with status {rc}")
-    return Result(keys_out, vals_out, sizes, pads, sample, spl, bof, pl)
+    return Result(keys_out, vals_out, sizes, pads, sample, spl, bof, pl, part)

@@ -28,6 +28,14 @@
  *   SS7 prefix      per-bucket counts and receive offsets (Fig. 1 step 9)
  *   SS8 route       order-preserving all-to-all (Fig. 1 steps 10-11)
  *   SS9 merge       stable multi-way merge of each bucket (Fig. 1 step 12)
+ * params.variant = OR_RAN runs procedure Sort_Ran_BSP (Fig. 2, Sec. 5.2)
+ * instead (random oversampling only): no local sort first; SS6 classifies
+ * every key by binary search of the splitters (Fig. 2 step 9) and groups the
+ * block by bucket, keeping input order; SS9 sorts each received bucket (Fig. 2
+ * step 12).  Its buckets and output are those of Sort_IRan_BSP.
+ * params.duplicates = OR_DUP_OFF compares records by (pad, phi) alone in the
+ * partition / classification: the paper's version without duplicate handling
+ * (Sec. 6.1), whose cost Sec. 6.4 measures.  Sorting stays by the total order.
  * Each superstep is a function of one processor id; all processors run it,
  * one after the other or on several host threads (params.threads), and the
  * next superstep starts only when every processor has finished (the barrier
@@ -61,6 +69,8 @@
 
 enum { OR_U32 = 0, OR_I32 = 1, OR_F32 = 2, OR_F64 = 3 };
 enum { OR_REGULAR = 0, OR_RANDOM = 1 };
+enum { OR_DUP_TAGS = 0, OR_DUP_OFF = 1 };
+enum { OR_DET_IRAN = 0, OR_RAN = 1 };
 
 /* one record of the total order, as reported to the caller */
 typedef struct {
@@ -77,6 +87,8 @@ typedef struct {
     int32_t sampling; /* OR_REGULAR or OR_RANDOM */
     int32_t threads;  /* host threads running the processors; 0 -> 1 */
     uint64_t seed;    /* random-mode sample seed */
+    int32_t duplicates; /* OR_DUP_TAGS (Sec. 5.1.1) or OR_DUP_OFF */
+    int32_t variant;    /* OR_DET_IRAN (Fig. 1 / Fig. 3) or OR_RAN (Fig. 2) */
 } oracle_params;
 
 /* the resolved parameters of one call */
@@ -137,6 +149,12 @@ static int elem_cmp(const void *a_, const void *b_) {
 
 static int elem_less(const elem *a, const elem *b) { return elem_cmp(a, b) < 0; }
 
+/* without duplicate handling: (pad, phi) only */
+static int elem_less_notag(const elem *a, const elem *b) {
+    if (a->pad != b->pad) return a->pad < b->pad;
+    return a->phi < b->phi;
+}
+
 /* ------------------------------------------------------------------ */
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)                   */
 
@@ -187,6 +205,9 @@ int oracle_plan_of(int64_t n, const oracle_params *prm, oracle_plan *pl) {
     if (!prm || !pl || n < 0 || prm->p < 1) return OR_EINVAL;
     if (prm->sampling != OR_REGULAR && prm->sampling != OR_RANDOM) return OR_EINVAL;
     if (prm->s < 0 || prm->runs < 0) return OR_EINVAL;
+    if (prm->duplicates != OR_DUP_TAGS && prm->duplicates != OR_DUP_OFF) return OR_EINVAL;
+    if (prm->variant != OR_DET_IRAN && prm->variant != OR_RAN) return OR_EINVAL;
+    if (prm->variant == OR_RAN && prm->sampling != OR_RANDOM) return OR_EINVAL;
     memset(pl, 0, sizeof(*pl));
     pl->n = n;
     pl->p = prm->p;
@@ -257,6 +278,8 @@ typedef struct {
     uint64_t seed;
     oracle_plan pl;
     int regular;
+    int dup_off;          /* compare by (pad, phi) alone in SS6 */
+    int ran;              /* Sort_Ran_BSP (Fig. 2) */
     elem **local;         /* local[k]: the records held by processor k */
     int64_t *len;         /* records held (keys and pads) */
     int64_t *nreal;       /* real keys held */
@@ -376,11 +399,49 @@ static void ss6_partition(machine *S, int64_t k) {
         int64_t lo = 0, hi = S->len[k];
         while (lo < hi) {
             int64_t mid = lo + (hi - lo) / 2;
-            if (elem_less(&local[k][mid], &Sk[k][i - 1])) lo = mid + 1;
+            const int less = S->dup_off ? elem_less_notag(&local[k][mid], &Sk[k][i - 1])
+                                        : elem_less(&local[k][mid], &Sk[k][i - 1]);
+            if (less) lo = mid + 1;
             else hi = mid;
         }
         ck[i] = lo;
     }
+}
+
+/* ---- SS6 of Sort_Ran_BSP: processor k finds the bucket of each of its keys
+ *      by binary search of the splitters (Fig. 2 step 9) -- the number of
+ *      splitters not above the key -- and groups its block by bucket, each
+ *      group in input order; segment i = group i ---- */
+static void ss6_classify(machine *S, int64_t k) {
+    elem **local = S->local, **Sk = S->Sk;
+    const int64_t p = S->pl.p, len = S->len[k];
+    int64_t *ck = S->c + k * (p + 1);
+    int64_t *b = malloc(sizeof(int64_t) * (size_t)(len ? len : 1));
+    elem *grouped = malloc(sizeof(elem) * (size_t)(len ? len : 1));
+    if (!b || !grouped) { free(b); free(grouped); fail(S); return; }
+    for (int64_t i = 0; i <= p; ++i) ck[i] = 0;
+    for (int64_t j = 0; j < len; ++j) {
+        /* bucket = #{i : S_i <= e} = first splitter index with e < S_i */
+        int64_t lo = 0, hi = p - 1;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            const int less = S->dup_off ? elem_less_notag(&local[k][j], &Sk[k][mid])
+                                        : elem_less(&local[k][j], &Sk[k][mid]);
+            if (less) hi = mid;
+            else lo = mid + 1;
+        }
+        b[j] = lo;
+        ck[lo + 1]++;
+    }
+    for (int64_t i = 0; i < p; ++i) ck[i + 1] += ck[i];
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)p);
+    if (!fill) { free(b); free(grouped); fail(S); return; }
+    for (int64_t i = 0; i < p; ++i) fill[i] = ck[i];
+    for (int64_t j = 0; j < len; ++j) grouped[fill[b[j]]++] = local[k][j];
+    free(fill);
+    free(b);
+    free(local[k]);
+    local[k] = grouped;
 }
 
 /* ---- SS7: counts of bucket i and the receive offsets of its segments
@@ -419,6 +480,27 @@ static void ss8_route(machine *S, int64_t i) {
 
 /* ---- SS9: processor i merges its received sorted segments stably (Fig. 1
  *      step 12; ties by source processor, Sec. 5.1.1) and emits its keys ---- */
+/* ---- SS9 of Sort_Ran_BSP: processor i sorts what it received (Fig. 2
+ *      step 12) and emits its keys ---- */
+static void ss9_sort(machine *S, int64_t i) {
+    const int64_t m = S->pl.m, M = S->pl.M;
+    elem *Z = S->Z[i];
+    const int64_t len = S->bucket_len[i];
+    qsort(Z, (size_t)len, sizeof(elem), elem_cmp);
+    int64_t out = S->out_off[i];
+    for (int64_t t = 0; t < len; ++t) {
+        const elem *e = &Z[t];
+        if (e->pad) continue;
+        put_key(S->dtype, S->keys_out, out, key_of_phi(S->dtype, e->phi));
+        if (S->vals_out) S->vals_out[out] = e->val;
+        if (S->bucket_of) {
+            int64_t k = (int64_t)(e->tag / (uint64_t)M), j = (int64_t)(e->tag % (uint64_t)M);
+            S->bucket_of[k * m + j] = (int32_t)i;
+        }
+        ++out;
+    }
+}
+
 static void ss9_merge(machine *S, int64_t i) {
     const int64_t p = S->pl.p, R = S->pl.R, m = S->pl.m, M = S->pl.M;
     const int64_t *c = S->c;
@@ -478,13 +560,16 @@ static void release(machine *S) {
  *   sample        plan.sample_size sorted sample records
  *   splitters     p-1 splitter records
  *   bucket_of     n bucket ids, indexed by the input position
+ *   partition     R*(p+1) entries c[k][i] at k*(p+1) + i: the first position
+ *                 of segment i in sorted block k (SS6; pads included).  With
+ *                 OR_RAN: the first position of group i in block k.
  * prm->threads host threads run the processors of each superstep (0 or 1:
  * one after the other); the result does not depend on it.
  */
 int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
                 const oracle_params *prm, void *keys_out, uint32_t *vals_out,
                 int64_t *bucket_sizes, int64_t *pad_sizes, oracle_record *sample,
-                oracle_record *splitters, int32_t *bucket_of) {
+                oracle_record *splitters, int32_t *bucket_of, int64_t *partition) {
     if (dtype < OR_U32 || dtype > OR_F64) return OR_EINVAL;
     oracle_plan pl;
     int rc = oracle_plan_of(n, prm, &pl);
@@ -500,6 +585,8 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     machine *S = &mc;
     S->dtype = dtype; S->keys = keys; S->vals = vals; S->seed = prm->seed; S->pl = pl;
     S->regular = pl.sampling == OR_REGULAR;
+    S->dup_off = prm->duplicates == OR_DUP_OFF;
+    S->ran = prm->variant == OR_RAN;
     S->keys_out = keys_out; S->vals_out = vals_out; S->pad_sizes = pad_sizes; S->bucket_of = bucket_of;
     S->local = calloc((size_t)R, sizeof(elem *));
     S->len = calloc((size_t)R, sizeof(int64_t));
@@ -524,8 +611,9 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     superstep(S, T, R, ss0_distribute);
     if (S->failed) { release(S); return OR_ENOMEM; }
 
-    /* ---- SS1: local sort on every processor (Fig. 1/3 step 3) ---- */
-    superstep(S, T, R, ss1_local_sort);
+    /* ---- SS1: local sort on every processor (Fig. 1/3 step 3; none in
+     *      Sort_Ran_BSP) ---- */
+    if (!S->ran) superstep(S, T, R, ss1_local_sort);
 
     /* ---- SS2: sample (Fig. 1 step 4 / Fig. 3 step 4) ---- */
     if (S->regular) {
@@ -560,8 +648,11 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     if (S->failed) { release(S); return OR_ENOMEM; }
 
     /* ---- SS6: partition by binary search of each splitter into the sorted
-     *      local keys (Sec. 5.1 step 9) ---- */
-    superstep(S, T, R, ss6_partition);
+     *      local keys (Sec. 5.1 step 9); Sort_Ran_BSP classifies every key
+     *      (Fig. 2 step 9) ---- */
+    superstep(S, T, R, S->ran ? ss6_classify : ss6_partition);
+    if (S->failed) { release(S); return OR_ENOMEM; }
+    if (partition) memcpy(partition, S->c, sizeof(int64_t) * (size_t)R * (size_t)(p + 1));
 
     /* ---- SS7: per-bucket counts and prefix sums (Fig. 1 step 9) ---- */
     superstep(S, T, p, ss7_prefix);
@@ -578,8 +669,9 @@ int oracle_sort(int dtype, const void *keys, const uint32_t *vals, int64_t n,
     superstep(S, T, R, free_block);  /* the routed records now live in Z */
 
     /* ---- SS9: stable multi-way merge of the received sorted segments
-     *      (Fig. 1 step 12; ties by source processor, Sec. 5.1.1) ---- */
-    superstep(S, T, p, ss9_merge);
+     *      (Fig. 1 step 12; ties by source processor, Sec. 5.1.1); in
+     *      Sort_Ran_BSP a sort of each received bucket (Fig. 2 step 12) ---- */
+    superstep(S, T, p, S->ran ? ss9_sort : ss9_merge);
     const int failed = S->failed;
     release(S);
     if (failed) return OR_ENOMEM;

@@ -409,3 +409,116 @@ def test_std_sort_baseline_sorts():
     for keys in (gen.uniform(100_000, 4, 1), gen.uniform_u32(50_000, 2), gen.gmm(30_000, seed=1)):
         for stable in (False, True):
             assert np.array_equal(oracle.std_sort(keys, stable=stable), np.sort(keys))
+
+
+# ------------------------------------- partition (Fig. 1 step 9), Sort_Ran_BSP (Fig. 2),
+#                                        and the version without duplicate handling
+
+def _partition_direct(keys, res):
+    """c[k][i] of every block: #{records of block k preceding S_i}, from numpy
+    comparisons of the typed keys and input positions; pads follow every key
+    and precede a pad splitter of a larger tag (Lemma 5.1's padding)."""
+    pl = res.plan
+    n, m, M, R, p = keys.shape[0], int(pl.m), int(pl.M), int(pl.R), int(pl.p)
+    padded = pl.sampling == oracle.REGULAR
+    out = np.zeros((R, p + 1), np.int64)
+    for k in range(R):
+        lo, hi = min(n, k * m), min(n, (k + 1) * m)
+        blk, pos = keys[lo:hi], np.arange(lo, hi)
+        held = M if padded else hi - lo
+        out[k, p] = held
+        for i, rec in enumerate(res.splitters, start=1):
+            if rec["pad"]:
+                # every key, and the pads of this block whose tag is smaller
+                tags = k * M + np.arange(hi - lo, held)
+                out[k, i] = (hi - lo) + int(np.count_nonzero(tags < int(rec["tag"])))
+                continue
+            g = _global_index(rec["tag"], pl)
+            v = keys[g]
+            out[k, i] = int(np.count_nonzero(blk < v)) + int(np.count_nonzero((blk == v) & (pos < g)))
+    return out
+
+
+PARTITION_CASES = [
+    ("uniform_regular", lambda: gen.uniform(5000, 8, 3), oracle.REGULAR, 8, 0, 0),
+    ("zipf_regular_pads", lambda: gen.zipf(4999, seed=5), oracle.REGULAR, 8, 16, 32),
+    ("equal_regular", lambda: np.full(3000, 7, np.int32), oracle.REGULAR, 4, 8, 8),
+    ("zipf_random", lambda: gen.zipf(6001, seed=6), oracle.RANDOM, 16, 0, 0),
+    ("gmm_random", lambda: gen.gmm(4000, seed=2), oracle.RANDOM, 8, 4, 3),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,p,runs,s", PARTITION_CASES, ids=[c[0] for c in PARTITION_CASES])
+def test_partition_is_the_direct_count(name, make, mode, p, runs, s):
+    keys = make()
+    res = oracle.sort(keys, p, s, runs, mode, 9, want_partition=True)
+    assert np.array_equal(res.partition, _partition_direct(keys, res))
+
+
+RAN_CASES = [
+    ("uniform_i32", lambda: gen.uniform(20000, 16, 1), 16, 0),
+    ("zipf_i32", lambda: gen.zipf(20000, seed=3), 32, 0),
+    ("equal_i32", lambda: np.full(5000, -3, np.int32), 8, 4),
+    ("gmm_f64", lambda: gen.gmm(8000, seed=7), 64, 16),
+    ("u32", lambda: gen.uniform_u32(7777, seed=4), 4, 2),
+]
+
+
+@pytest.mark.parametrize("name,make,p,runs", RAN_CASES, ids=[c[0] for c in RAN_CASES])
+def test_sort_ran_bsp_equals_sort_iran_bsp(name, make, p, runs):
+    """Sort_Ran_BSP (Fig. 2: classify every key, route, sort each bucket) and
+    Sort_IRan_BSP (Fig. 3: sort, partition by binary search, route, merge)
+    use the same splitters, so they give the same buckets, per-key buckets and
+    output; the Fig. 2 grouping of block k puts keys of bucket < i first."""
+    keys = make()
+    vals = np.arange(keys.shape[0], dtype=np.uint32)
+    a = oracle.sort(keys, p, 0, runs, oracle.RANDOM, 11, vals=vals, want_bucket_of=True)
+    b = oracle.sort(keys, p, 0, runs, oracle.RANDOM, 11, vals=vals, want_bucket_of=True,
+                    variant=oracle.RAN, want_partition=True)
+    assert np.array_equal(a.keys, b.keys) and np.array_equal(a.vals, b.vals)
+    assert np.array_equal(a.bucket_sizes, b.bucket_sizes)
+    assert np.array_equal(a.bucket_of, b.bucket_of)
+    assert np.array_equal(a.splitters, b.splitters)
+    check_against_direct(keys, b)
+    m, n = int(b.plan.m), keys.shape[0]
+    for k in range(int(b.plan.R)):
+        bof = b.bucket_of[min(n, k * m):min(n, (k + 1) * m)]
+        want = np.searchsorted(np.sort(bof), np.arange(p + 1), side="left")
+        assert np.array_equal(b.partition[k], want)
+
+
+def test_sort_ran_bsp_needs_random_sampling():
+    with pytest.raises(ValueError):
+        oracle.sort(gen.uniform(1000, 4, 1), 4, 0, 0, oracle.REGULAR, variant=oracle.RAN)
+
+
+DUP_CASES = [
+    ("zipf_regular", lambda: gen.zipf(30000, seed=8), oracle.REGULAR, 16, 0, 0),
+    ("zipf_random", lambda: gen.zipf(30000, seed=8), oracle.RANDOM, 16, 0, 0),
+    ("equal_regular_pads", lambda: np.full(3001, 5, np.int32), oracle.REGULAR, 4, 8, 8),
+    ("uniform_random", lambda: gen.uniform(20000, 16, 2), oracle.RANDOM, 32, 0, 0),
+    ("f32_regular", lambda: gen.gmm(9000, seed=1).astype(np.float32), oracle.REGULAR, 8, 0, 0),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,p,runs,s", DUP_CASES, ids=[c[0] for c in DUP_CASES])
+def test_without_duplicate_handling_buckets_are_value_counts(name, make, mode, p, runs, s):
+    """Without the tags (Sec. 6.1's version without duplicate handling) the
+    sample and splitters are unchanged, the output is the same stable sort,
+    and a key's bucket is the number of splitters whose key is not above it
+    (numpy searchsorted on the splitters' typed keys); every pad, equal to
+    the pad splitters, lands in the last bucket."""
+    keys = make()
+    vals = np.arange(keys.shape[0], dtype=np.uint32)
+    t = oracle.sort(keys, p, s, runs, mode, 4, vals=vals, want_bucket_of=True)
+    d = oracle.sort(keys, p, s, runs, mode, 4, vals=vals, want_bucket_of=True, duplicates=oracle.DUP_OFF)
+    assert np.array_equal(t.sample, d.sample) and np.array_equal(t.splitters, d.splitters)
+    assert np.array_equal(t.keys, d.keys) and np.array_equal(t.vals, d.vals)
+    real = [keys[_global_index(r["tag"], d.plan)] for r in d.splitters if not r["pad"]]
+    want = np.searchsorted(np.array(real, keys.dtype), keys, side="right")
+    assert np.array_equal(d.bucket_of, want)
+    assert np.array_equal(d.bucket_sizes, np.bincount(want, minlength=p))
+    assert d.pad_sizes[:-1].sum() == 0
+    assert d.pad_sizes[-1] == (int(d.plan.R) * int(d.plan.M) - keys.shape[0] if mode == oracle.REGULAR else 0)
+    if name.startswith("zipf") or name.startswith("equal"):
+        assert not np.array_equal(t.bucket_sizes, d.bucket_sizes)

@@ -28,8 +28,11 @@ MUTANTS = {
     "splitter_rank_off_by_one": ("Y[i * pl.q - 1]", "Y[i * pl.q]"),
     "tag_order_reversed": ("if (a->tag != b->tag) return a->tag < b->tag ? -1 : 1;",
                            "if (a->tag != b->tag) return a->tag < b->tag ? 1 : -1;"),
-    "splitter_to_lower_bucket": ("if (elem_less(&local[k][mid], &Sk[k][i - 1])) lo = mid + 1;",
-                                 "if (!elem_less(&Sk[k][i - 1], &local[k][mid])) lo = mid + 1;"),
+    "splitter_to_lower_bucket": (": elem_less(&local[k][mid], &Sk[k][i - 1]);",
+                                 ": !elem_less(&Sk[k][i - 1], &local[k][mid]);"),
+    "classify_splitter_to_lower_bucket": (": elem_less(&local[k][j], &Sk[k][mid]);",
+                                          ": !elem_less(&Sk[k][mid], &local[k][j]);"),
+    "duplicates_off_keeps_tags": ("S->dup_off = prm->duplicates == OR_DUP_OFF;", "S->dup_off = 0;"),
     "int32_sign_ignored": ("case OR_I32: return u ^ 0x80000000u;", "case OR_I32: return u;"),
     "pads_counted_as_keys": ("if (local[k][t].pad) { if (pad_sizes)", "if (0) { if (pad_sizes)"),
     "random_stream_shifted": ("(unsigned __int128)oracle_draw(seed, j)",
@@ -49,14 +52,14 @@ def _build(mutant_src, outdir):
     lib = ctypes.CDLL(so)
     P = ctypes.c_void_p
     lib.oracle_sort.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, ctypes.POINTER(oracle.Params),
-                                P, P, P, P, P, P, P]
+                                P, P, P, P, P, P, P, P]
     lib.oracle_sort.restype = ctypes.c_int
     lib.oracle_position.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64]
     lib.oracle_position.restype = ctypes.c_int64
     return lib
 
 
-def _run(lib, keys, p, s, runs, mode, seed, vals):
+def _run(lib, keys, p, s, runs, mode, seed, vals, duplicates=oracle.DUP_TAGS, variant=oracle.DET_IRAN):
     n = keys.shape[0]
     pl = oracle.plan(n, p, s, runs, mode, seed)
     out = np.empty_like(keys)
@@ -66,10 +69,10 @@ def _run(lib, keys, p, s, runs, mode, seed, vals):
     smp = np.zeros(pl.sample_size, oracle.RECORD_DTYPE)
     spl = np.zeros(pl.p - 1, oracle.RECORD_DTYPE)
     bof = np.full(n, -1, np.int32)
-    prm = oracle.make_params(p, s, runs, mode, seed)
+    prm = oracle.make_params(p, s, runs, mode, seed, duplicates=duplicates, variant=variant)
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
     rc = lib.oracle_sort(oracle.DTYPE_CODE[keys.dtype], ptr(keys), ptr(vals), n, ctypes.byref(prm),
-                         ptr(out), ptr(vout), ptr(sizes), ptr(pads), ptr(smp), ptr(spl), ptr(bof))
+                         ptr(out), ptr(vout), ptr(sizes), ptr(pads), ptr(smp), ptr(spl), ptr(bof), None)
     return rc, pl, out, vout, sizes, pads, smp, spl, bof
 
 
@@ -101,6 +104,22 @@ def _pins_pass(lib):
                 return False
             if not np.array_equal(bof, np.searchsorted(b[1:-1], stable_ranks(keys), side="right")):
                 return False
+    # Sort_Ran_BSP (Fig. 2) against the direct count; without duplicate
+    # handling, buckets by the splitters' key values alone
+    keys = gen.zipf(3000, seed=4)
+    vals = np.arange(keys.shape[0], dtype=np.uint32)
+    rc, pl, out, vout, sizes, pads, smp, spl, bof = _run(lib, keys, 8, 0, 0, oracle.RANDOM, 5, vals,
+                                                         variant=oracle.RAN)
+    b = direct_counts(keys, spl, pl)
+    if rc or not np.array_equal(bof, np.searchsorted(b[1:-1], stable_ranks(keys), side="right")):
+        return False
+    for mode in (oracle.REGULAR, oracle.RANDOM):
+        rc, pl, out, vout, sizes, pads, smp, spl, bof = _run(lib, keys, 8, 0, 0, mode, 5, vals,
+                                                             duplicates=oracle.DUP_OFF)
+        real = np.array([keys[k * int(pl.m) + j] for k, j in
+                         (divmod(int(r["tag"]), int(pl.M)) for r in spl if not r["pad"])], keys.dtype)
+        if rc or not np.array_equal(bof, np.searchsorted(real, keys, side="right")):
+            return False
     # numpy's Philox stream
     bg = np.random.Philox(key=np.array([5, 0], np.uint64), counter=np.array([2**64 - 1] * 4, np.uint64))
     want = [int(v) >> 44 for v in bg.random_raw(16)]
