@@ -41,6 +41,19 @@ WORKLOADS = {
                                             make=lambda n, p, seed: gen.uniform(n, p, seed)),
     "zipf_2e28_int32_pairs_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=True,
                                                make=lambda n, p, seed: gen.zipf(n, seed=seed)),
+    # the regular configurations ended by the paper's merge (Fig. 1 steps 9-12),
+    # with the bucket-sort final step timed beside them on the same inputs
+    "uniform_2e28_int32_p4096_regular_merge": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096,
+                                                  pairs=False, final_step=1, compare="sort",
+                                                  make=lambda n, p, seed: gen.uniform(n, p, seed)),
+    "zipf_2e28_int32_pairs_p4096_regular_merge": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096,
+                                                     pairs=True, final_step=1, compare="sort",
+                                                     make=lambda n, p, seed: gen.zipf(n, seed=seed)),
+    # the cost of the duplicate handling (Sec. 6.4 measures it): the headline
+    # sort without the tie-break, and with it (timed beside) on the same keys
+    "uniform_2e28_int32_p4096_random_nodup": dict(n=1 << 28, p=4096, sampling=1, s=0, runs=0, pairs=False,
+                                                 duplicates=1, compare="tags",
+                                                 make=lambda n, p, seed: gen.uniform(n, p, seed)),
     # the 2^28 workload's kernels on a quarter of the data, for full ncu
     # captures (inputs still larger than L2)
     "uniform_2e26_int32_p4096_random": dict(n=1 << 26, p=4096, sampling=1, s=0, runs=0, pairs=False,
@@ -87,6 +100,9 @@ PHASES = ["sample", "sample_sort", "splitters", "route", "bucket_sort"]
 PHASE_KERNEL = {("route", False): "route_keys_kernel", ("bucket_sort", False): "bucket_keys32_kernel",
                 ("route", True): "route_kernel", ("bucket_sort", True): "bucket_sort_kernel"}
 PHASE_KERNEL_F64 = {"bucket_sort": "bucket_keys_kernel"}
+# the variant timed beside a workload: (label, the parameters that change)
+COMPARE = {"tree": ("tree", dict(classify=0)), "sort": ("bucket_sort_final_step", dict(final_step=0)),
+           "tags": ("with_duplicate_handling", dict(duplicates=0))}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
 # ncu capture (profiles/*.md), valid while the kernel source is unchanged:
@@ -221,7 +237,7 @@ def oracle_rate(wl, budget_s=12.0, seed=1, threads=1):
         vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
         t0 = time.perf_counter()
         oracle.sort(keys, wl["p"], wl["s"], wl["runs"], wl["sampling"], seed=seed, vals=vals, want_sample=False,
-                    threads=threads)
+                    threads=threads, duplicates=wl.get("duplicates", 0))
         t = time.perf_counter() - t0
         if t > budget_s / 4 or n >= wl["n"]:
             return n / t, n, wl["s"], wl["runs"], t
@@ -274,7 +290,8 @@ def run_reference(args, wl, name):
     vals = np.arange(n, dtype=np.uint32) if wl["pairs"] else None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.sort(keys, wl["p"], s, runs, wl["sampling"], seed=1, vals=vals, want_sample=False, threads=T)
+        oracle.sort(keys, wl["p"], s, runs, wl["sampling"], seed=1, vals=vals, want_sample=False, threads=T,
+                    duplicates=wl.get("duplicates", 0))
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -309,8 +326,7 @@ def run_gpu(args, wl, name):
     n, p = wl["n"], wl["p"]
     f64 = wl.get("dtype") == "f64"
     code = bsps.BSPS_F64 if f64 else bsps.BSPS_I32
-    prm = bsps.make_params(p, s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
-                           refine=args.refine or wl.get("refine", 0), classify=wl.get("classify", 0))
+    prm = params_of(bsps, wl, args, 1 + rank)
     plan = bsps.bsps_get_plan(n, code, prm, wl["pairs"])
     keys_h = np.ascontiguousarray(wl["make"](n, p, 1 + rank))
     kin = torch.from_numpy(keys_h).to(dev)
@@ -381,7 +397,8 @@ def run_gpu(args, wl, name):
         import oracle
         t0 = time.perf_counter()
         ref = oracle.sort(keys_h, p, wl["s"], wl["runs"], wl["sampling"], seed=prm.seed, want_sample=False,
-                          vals=np.arange(n, dtype=np.uint32) if wl["pairs"] else None, threads=host_threads())
+                          vals=np.arange(n, dtype=np.uint32) if wl["pairs"] else None, threads=host_threads(),
+                          duplicates=wl.get("duplicates", 0))
         if not np.array_equal(sizes.cpu().numpy(), ref.bucket_sizes):
             raise RuntimeError("bucket sizes differ from the oracle's")
         if wl["pairs"] and not np.array_equal(vout.cpu().numpy().view(np.uint32), ref.vals):
@@ -391,8 +408,9 @@ def run_gpu(args, wl, name):
                     "oracle_s": round(time.perf_counter() - t0, 1)}
         del ref
     compare = None
-    if wl.get("compare") == "tree":
-        compare = compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st, stream, elapsed_ms)
+    if wl.get("compare"):
+        compare = compare_variant(args, bsps, kin, vin, kout, vout, sizes, n, code, wl, rank, st, stream,
+                                  elapsed_ms)
 
     # end to end through the C ABI with host buffers: H2D of the keys, the sort,
     # D2H of the sorted keys, every step
@@ -406,31 +424,57 @@ def run_gpu(args, wl, name):
                   e2e_steps, total_launches, clk, compare, verified)
 
 
-def compare_tree(args, bsps, kin, kout, sizes, n, code, wl, rank, st_learned, stream, learned_ms):
-    """The same sort with the splitter tree: time, and identical output."""
+def params_of(bsps, wl, args, seed, **override):
+    kw = dict(s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=seed,
+              refine=args.refine or wl.get("refine", 0), classify=wl.get("classify", 0),
+              final_step=wl.get("final_step", 0), duplicates=wl.get("duplicates", 0))
+    kw.update(override)
+    return bsps.make_params(wl["p"], **kw)
+
+
+def compare_variant(args, bsps, kin, vin, kout, vout, sizes, n, code, wl, rank, st_this, stream, this_ms):
+    """The same sort with the variant COMPARE names (the splitter tree, the
+    bucket-sort final step, the duplicate handling): time, and identical
+    sorted output (and bucket sizes, except without the tie-break)."""
     import torch
-    prm = bsps.make_params(wl["p"], s=wl["s"], runs=wl["runs"], sampling=wl["sampling"], seed=1 + rank,
-                           refine=args.refine or wl.get("refine", 0), classify=0)
-    plan = bsps.bsps_get_plan(n, code, prm, False)
+    label, override = COMPARE[wl["compare"]]
+    prm = params_of(bsps, wl, args, 1 + rank, **override)
+    plan = bsps.bsps_get_plan(n, code, prm, vin is not None)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=kin.device)
     out = torch.empty_like(kout)
+    vo = torch.empty_like(vout) if vin is not None else None
     sz = torch.empty_like(sizes)
+
+    def one():
+        if vin is None:
+            assert bsps.bsps_sort_keys(kin, out, n, code, prm, sz, ws) == 0
+        else:
+            assert bsps.bsps_sort_pairs(kin, vin, out, vo, n, code, prm, sz, ws) == 0
     for _ in range(args.warmup):
-        assert bsps.bsps_sort_keys(kin, out, n, code, prm, sz, ws) == 0
+        one()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        assert bsps.bsps_sort_keys(kin, out, n, code, prm, sz, ws) == 0
+        one()
     e1.record(stream)
     torch.cuda.synchronize()
-    tree_ms = e0.elapsed_time(e1) / args.steps
-    same = bool(torch.equal(out.view(torch.int64) if code == bsps.BSPS_F64 else out,
-                            kout.view(torch.int64) if code == bsps.BSPS_F64 else kout)) and bool(torch.equal(sz, sizes))
-    return {"tree_ms_per_step": tree_ms, "learned_ms_per_step": learned_ms / args.steps,
-            "learned_vs_tree": tree_ms / (learned_ms / args.steps), "identical_output": same,
-            "mispredicted_frac": st_learned.mispredicted / n,
-            "correction_steps_per_key": st_learned.correction_steps / n}
+    if bsps.bsps_read_stats(ws).status:
+        raise RuntimeError("the compared variant reported an error")
+    other_ms = e0.elapsed_time(e1) / args.steps
+    as_bits = (lambda t: t.view(torch.int64)) if code == bsps.BSPS_F64 else (lambda t: t)
+    same = bool(torch.equal(as_bits(out), as_bits(kout)))
+    if vin is not None:
+        same = same and bool(torch.equal(vo, vout))
+    same_sizes = bool(torch.equal(sz, sizes))
+    this = "learned" if wl["compare"] == "tree" else "this"
+    res = {"other": label, f"{label}_ms_per_step": other_ms, f"{this}_ms_per_step": this_ms / args.steps,
+           f"{this}_vs_{label}": other_ms / (this_ms / args.steps), "identical_output": same,
+           "identical_bucket_sizes": same_sizes}
+    if wl["compare"] == "tree":
+        res["mispredicted_frac"] = st_this.mispredicted / n
+        res["correction_steps_per_key"] = st_this.correction_steps / n
+    return res
 
 
 def per_step_of(phase_ms, args):
@@ -497,11 +541,21 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     pk, pk_kind = peaks()
     key_bytes = 8 if wl.get("dtype") == "f64" else 4
     kb = key_bytes + (4 if wl["pairs"] else 0)
-    dom = max(("route", "bucket_sort"), key=lambda k: per_step[k])
-    kern = PHASE_KERNEL[(dom, bool(wl["pairs"]))]
-    if key_bytes == 8 and not wl["pairs"]:
-        kern = PHASE_KERNEL_F64.get(dom, kern)
-    alg_bytes = n * 2 * kb
+    merge = wl.get("final_step", 0) == 1
+    # (kernel, algorithmic bytes) of every phase that moves all the keys
+    model = {}
+    if wl["sampling"] == 0:  # the block sort reads every key (and keeps the sorted blocks for the merge)
+        model["sample"] = ("run_sample_keys_kernel", n * (2 * kb if merge else key_bytes))
+    if merge:
+        model["bucket_sort"] = ("merge_bucket_kernel", n * 2 * kb)
+    else:
+        for ph in ("route", "bucket_sort"):
+            kern = PHASE_KERNEL[(ph, bool(wl["pairs"]))]
+            if key_bytes == 8 and not wl["pairs"]:
+                kern = PHASE_KERNEL_F64.get(ph, kern)
+            model[ph] = (kern, n * 2 * kb)
+    dom = max(model, key=lambda k: per_step[k])
+    kern, alg_bytes = model[dom]
     achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
     traffic = None
     if kern in NCU_TRAFFIC and NCU_TRAFFIC[kern][1] == source_hash(KERNEL_SOURCE[kern]) and \
@@ -510,7 +564,8 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     ms_step = elapsed_ms / args.steps
     value = world * n / (ms_step * 1e-3)
     rec = 8 if key_bytes == 4 else 16
-    b_alg = 4 * kb + plan.sample_size * (key_bytes + 2 * rec) / n + (kb if wl["sampling"] == 0 else 0)
+    b_alg = 4 * kb + plan.sample_size * (key_bytes + 2 * rec) / n + \
+        (key_bytes if wl["sampling"] == 0 and not merge else 0)
     cpu = None
     if world == 1 and not args.no_baseline and wl.get("dtype") != "f64":
         cpu = cpu_baselines(wl, p)
@@ -522,6 +577,8 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
                    "s": plan.s, "runs": plan.R, "sample_size": plan.sample_size, "pairs": wl["pairs"],
                    "refine": plan.refine, "bucket_cluster": plan.bucket_cluster,
                    "classify": "learned" if wl.get("classify") else "tree",
+                   "final_step": "merge" if merge else "bucket_sort",
+                   "duplicate_handling": not wl.get("duplicates", 0),
                    "l2": "inputs (1 GiB) larger than L2 (126 MB); no flush",
                    "parallelism": f"independent sorts x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -543,7 +600,7 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
                   "imbalance": st.max_bucket / (n / p) - 1},
     }
     if compare is not None:
-        line["learned_vs_tree"] = compare
+        line["learned_vs_tree" if wl["compare"] == "tree" else "compare"] = compare
     if verified is not None:
         line["verified"] = verified
     print(json.dumps(line), flush=True)
@@ -717,7 +774,7 @@ def run_batched(args, wl, name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))

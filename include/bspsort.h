@@ -46,6 +46,14 @@ typedef enum { BSPS_REGULAR = 0, BSPS_RANDOM = 1 } bsps_sampling;
 /* classification of keys against the splitters (Fig. 2 step 9) */
 typedef enum { BSPS_TREE = 0, BSPS_LEARNED = 1 } bsps_classify;
 
+/* the final step: sort every bucket (Fig. 2 step 12), or keep the sorted
+ * blocks and merge each bucket's segments (Fig. 1 steps 9-12) */
+typedef enum { BSPS_FINAL_SORT = 0, BSPS_FINAL_MERGE = 1 } bsps_final;
+
+/* duplicate keys: ties broken by input position (Sec. 5.1.1), or keys
+ * compared by value alone (the paper's version without duplicate handling) */
+typedef enum { BSPS_DUP_TAGS = 0, BSPS_DUP_OFF = 1 } bsps_duplicates;
+
 #define BSPS_OK 0
 #define BSPS_ERR_INVALID_ARG (-1)
 #define BSPS_ERR_WORKSPACE_TOO_SMALL (-2)
@@ -76,6 +84,26 @@ typedef enum { BSPS_TREE = 0, BSPS_LEARNED = 1 } bsps_classify;
  *   capacity_pct  random mode: capacity of each bucket region in percent of
  *             the mean sub-bucket size (0 -> automatic).  Regular mode ignores
  *             it and uses the exact bound of Lemma 5.1.
+ *   final     bsps_final.  BSPS_FINAL_MERGE ends Sort_Det_BSP as the paper
+ *             does: the blocks sorted for the regular sample (Fig. 1 step 3)
+ *             are kept, every splitter is located in every sorted block by
+ *             binary search (step 9: block k's segment of bucket i is
+ *             [c[k][i], c[k][i+1])), and each bucket's segments, taken in
+ *             block order (step 11), are merged stably, ties going to the
+ *             earlier block (step 12; Sec. 5.1.1).  The results are those of
+ *             BSPS_FINAL_SORT.  It requires regular sampling, 4-byte keys,
+ *             R <= 8192, refine 0 or 1 and tree classification
+ *             (BSPS_ERR_INVALID_ARG otherwise), and a bucket bound of Lemma
+ *             5.1 of at most 131,072 keys (BSPS_ERR_TOO_LARGE otherwise).
+ *   duplicates  bsps_duplicates.  BSPS_DUP_OFF compares keys by value
+ *             alone: a key goes to bucket #{i : phi(S_i) <= phi(key)}, every
+ *             key equal to a splitter in the highest such bucket.  It is the
+ *             baseline against which the paper measures the cost of its
+ *             duplicate handling (Sec. 6.1, Sec. 6.4).  The sorted output is
+ *             unchanged; bucket sizes differ when keys repeat, and the bounds
+ *             of Lemma 5.1 and Claim 5.1 no longer hold, so many equal keys
+ *             overflow a bucket (BSPS_ERR_BUCKET_OVERFLOW from
+ *             bsps_read_stats).
  */
 typedef struct {
     int32_t p;
@@ -86,6 +114,8 @@ typedef struct {
     uint64_t seed;
     int32_t refine;
     int32_t capacity_pct;
+    int32_t final_step;
+    int32_t duplicates;
 } bsps_params;
 
 /* A sample or splitter record of the total order: (pad, phi, tag), tag =
@@ -137,7 +167,11 @@ typedef struct {
  *     expire; wait_polls bounds the polls of one wait (0: the default bound,
  *     about a second).  An expired wait records BSPS_ERR_DEVICE_TIMEOUT,
  *     which bsps_read_stats returns; the call's output is then undefined but
- *     every access stays inside the caller's buffers. */
+ *     every access stays inside the caller's buffers.
+ *   partition: with BSPS_FINAL_MERGE, a DEVICE buffer of (p+1)*R uint32 that
+ *     receives the partition of Fig. 1 step 9: entry i*R + k is the number of
+ *     keys of sorted block k that precede splitter S_i (pads excluded; row 0
+ *     is 0, row p the block's key count). */
 #define BSPS_PHASES 6
 typedef struct {
     bsps_record *sample;     /* plan.sample_size records, sorted */
@@ -150,6 +184,7 @@ typedef struct {
     float *mlp_loss;         /* learned classifier: training loss before and after */
     int32_t stall_tile;      /* test hook (see above); 0: none */
     uint32_t wait_polls;     /* test hook (see above); 0: the default bound */
+    uint32_t *partition;     /* (p+1)*R entries, BSPS_FINAL_MERGE only */
 } bsps_debug;
 
 /*
@@ -324,7 +359,8 @@ int bsps_noalloc_read_stats(bsps_stats *stats, void *stream);
  *   sizes, instance i's p_i sizes starting at entry h_base[i] from
  *   bsps_batch_bucket_base().
  * Keys are 32- or 64-bit (the on-chip path takes 32-bit keys only).
- * Errors: BSPS_ERR_INVALID_ARG (bad offsets, num < 0, in == out, bad table),
+ * Errors: BSPS_ERR_INVALID_ARG (bad offsets, num < 0, in == out, bad table,
+ * prm->final_step or prm->duplicates other than their defaults),
  * BSPS_ERR_WORKSPACE_TOO_SMALL, BSPS_ERR_TOO_LARGE (an instance too large
  * for bsps_sort_keys), BSPS_ERR_CAPTURE, BSPS_ERR_CUDA.  Device-side statuses of all instances
  * (overflow, timeouts) are merged into the batch status that

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "libbspsort.so")
 BSPS_U32, BSPS_I32, BSPS_F32, BSPS_F64 = 0, 1, 2, 3
 BSPS_REGULAR, BSPS_RANDOM = 0, 1
 BSPS_TREE, BSPS_LEARNED = 0, 1
+BSPS_FINAL_SORT, BSPS_FINAL_MERGE = 0, 1
+BSPS_DUP_TAGS, BSPS_DUP_OFF = 0, 1
 BSPS_OK = 0
 BSPS_ERR_INVALID_ARG = -1
 BSPS_ERR_WORKSPACE_TOO_SMALL = -2
@@ -41,7 +43,8 @@ MLP_PARAMS = 1153
 class bsps_params(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("runs", ctypes.c_int32), ("s", ctypes.c_int64),
                 ("sampling", ctypes.c_int32), ("classify", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("refine", ctypes.c_int32), ("capacity_pct", ctypes.c_int32)]
+                ("refine", ctypes.c_int32), ("capacity_pct", ctypes.c_int32),
+                ("final_step", ctypes.c_int32), ("duplicates", ctypes.c_int32)]
 
 
 class bsps_record(ctypes.Structure):
@@ -78,7 +81,8 @@ class bsps_debug(ctypes.Structure):
                 ("phase_events", ctypes.POINTER(ctypes.c_void_p)),
                 ("launches", ctypes.POINTER(ctypes.c_int32)),
                 ("mlp_params", ctypes.c_void_p), ("mlp_loss", ctypes.c_void_p),
-                ("stall_tile", ctypes.c_int32), ("wait_polls", ctypes.c_uint32)]
+                ("stall_tile", ctypes.c_int32), ("wait_polls", ctypes.c_uint32),
+                ("partition", ctypes.c_void_p)]
 
 
 _lib = None
@@ -155,9 +159,9 @@ def dtype_code(t) -> int:
 
 
 def make_params(p, s=0, runs=0, sampling=BSPS_REGULAR, classify=BSPS_TREE, seed=0, refine=0,
-                capacity_pct=0) -> bsps_params:
+                capacity_pct=0, final_step=BSPS_FINAL_SORT, duplicates=BSPS_DUP_TAGS) -> bsps_params:
     return bsps_params(int(p), int(runs), int(s), int(sampling), int(classify), int(seed) & (2**64 - 1),
-                       int(refine), int(capacity_pct))
+                       int(refine), int(capacity_pct), int(final_step), int(duplicates))
 
 
 # ----------------------------------------------------------------- entry points
@@ -212,12 +216,13 @@ def bsps_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, dtype, params, buck
 def bsps_sort_debug(keys_in, vals_in, keys_out, vals_out, n, dtype, params, bucket_sizes, workspace,
                     sample=None, splitters=None, bucket_of=None, pad_sizes=None, phase_events=None,
                     launches=None, mlp_params=None, mlp_loss=None, stall_tile=0, wait_polls=0,
-                    stream=None) -> int:
+                    partition=None, stream=None) -> int:
     """phase_events: BSPS_PHASES recorded torch.cuda.Event objects (or raw handles);
     launches: a ctypes.c_int32 that receives the number of kernels launched;
-    stall_tile, wait_polls: the test hooks of the bounded waits (include/bspsort.h)."""
+    stall_tile, wait_polls: the test hooks of the bounded waits (include/bspsort.h);
+    partition: (p+1)*R uint32 entries of the merge final step's partition."""
     dbg = bsps_debug(_ptr(sample), _ptr(splitters), _ptr(bucket_of), _ptr(pad_sizes), None, None,
-                     _ptr(mlp_params), _ptr(mlp_loss), int(stall_tile), int(wait_polls))
+                     _ptr(mlp_params), _ptr(mlp_loss), int(stall_tile), int(wait_polls), _ptr(partition))
     if phase_events is not None:
         handles = [e if isinstance(e, int) else e.cuda_event for e in phase_events]
         assert len(handles) == BSPS_PHASES and all(handles), "events must exist (record them once first)"

@@ -36,6 +36,11 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     if (prm->sampling != BSPS_REGULAR && prm->sampling != BSPS_RANDOM) return BSPS_ERR_INVALID_ARG;
     if (prm->classify != BSPS_TREE && prm->classify != BSPS_LEARNED) return BSPS_ERR_INVALID_ARG;
     if (prm->refine != 0 && !is_pow2(prm->refine)) return BSPS_ERR_INVALID_ARG;
+    if (prm->final_step != BSPS_FINAL_SORT && prm->final_step != BSPS_FINAL_MERGE) return BSPS_ERR_INVALID_ARG;
+    if (prm->duplicates != BSPS_DUP_TAGS && prm->duplicates != BSPS_DUP_OFF) return BSPS_ERR_INVALID_ARG;
+    if (prm->final_step == BSPS_FINAL_MERGE &&
+        (prm->sampling != BSPS_REGULAR || dtype == BSPS_F64 || prm->refine > 1 || prm->classify != BSPS_TREE))
+        return BSPS_ERR_INVALID_ARG;
     if (n >= ((int64_t)1 << 30)) return BSPS_ERR_TOO_LARGE;
     std::memset(&pl, 0, sizeof(pl));
     pl.n = n;
@@ -43,6 +48,9 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     pl.R = prm->runs > 0 ? prm->runs : prm->p;
     pl.sampling = prm->sampling;
     pl.classify = prm->classify;
+    pl.dup_off = prm->duplicates == BSPS_DUP_OFF;
+    pl.merge = prm->final_step == BSPS_FINAL_MERGE;
+    if (pl.merge && pl.R > merge_runs_max()) return BSPS_ERR_INVALID_ARG;
     pl.dtype = dtype;
     pl.pairs = pairs;
     pl.seed = prm->seed;
@@ -79,7 +87,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         return pl.sampling == BSPS_RANDOM ? 1.0 + 5.0 / std::sqrt((double)std::max<int64_t>(1, pl.Q / B))
                                           : 1.25;
     };
-    int64_t B = prm->refine;
+    int64_t B = pl.merge ? 1 : prm->refine;
     if (B == 0) {
         B = 1;
         while (B * 2 <= pl.Q && (double)n / (pl.p * B) * headroom(B) > 8.0 * cap_cta) B *= 2;
@@ -126,8 +134,14 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         pl.cap = std::min<int64_t>(std::max<int64_t>(n, 1), (int64_t)std::ceil((double)n / pl.P * pct) + 64);
         pl.run_cl = 1;
     }
+    if (pl.merge) {
+        // one cluster merges a whole bucket: sized by the bound of Lemma 5.1
+        pl.bucket_cl = merge_cluster(pl);
+        if (pl.bucket_cl == 0) return BSPS_ERR_TOO_LARGE;
+        pl.cap = merge_capacity(pl.bucket_cl);
+    }
     pl.cap = (pl.cap + 3) & ~int64_t(3);  // 16-byte aligned regions
-    if ((double)pl.P * pl.cap >= 4.0e9) return BSPS_ERR_TOO_LARGE;
+    if (!pl.merge && (double)pl.P * pl.cap >= 4.0e9) return BSPS_ERR_TOO_LARGE;
     pl.tiles = (n + kRouteTile - 1) / kRouteTile;
     pl.lsd_tiles = (pl.sample_size + kLsdTile - 1) / kLsdTile;
     pl.lsd_npos = 4 + pl.key_bytes;
@@ -147,16 +161,22 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(pl.P * 4);
     take((kLutCells + 2) * 2);
     take(64);
-    take(pairs ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
-    take(pairs ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
+    const bool look_back = pairs && !pl.merge;
+    take(look_back ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
+    take(look_back ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     take(pl.P * 4);
     take(pl.P * 4); take(pl.P * 4);
     take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
-    take(pl.P * pl.cap * pl.key_bytes + 64);
-    take(pairs ? pl.P * pl.cap * 4 : 0);
+    const int64_t region_keys = pl.merge ? n : pl.P * pl.cap;  // the sorted blocks, or the bucket regions
+    take(region_keys * pl.key_bytes + 64);
+    take(pairs ? region_keys * 4 : 0);
     take(pl.P * 4);
     take((pl.P + 1) * 8);
     take(pl.P * 4);
+    if (pl.merge) {
+        take(pl.sample_size * 4); take(pl.sample_size * 4);
+        take((pl.p + 1) * pl.R * 4);
+    }
     if (pl.classify == BSPS_LEARNED) {
         take(kParams * 4);
         take((int64_t)kMlpGridMax * (kParams + 1) * 4);
@@ -190,17 +210,26 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.vtag = (uint32_t *)take(pl.P * 4);
     l.lut = (uint16_t *)take((kLutCells + 2) * 2);
     l.lutp = take(64);
-    l.state = (uint32_t *)take(pl.pairs ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
-    l.ids = (uint16_t *)take(pl.pairs ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
+    const bool look_back = pl.pairs && !pl.merge;
+    l.state = (uint32_t *)take(look_back ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
+    l.ids = (uint16_t *)take(look_back ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     l.cursor = (uint32_t *)take(pl.P * 4);
     l.retry_flag = (uint32_t *)take(pl.P * 4);
     l.retry_list = (uint32_t *)take(pl.P * 4);
     l.run_retry = (uint32_t *)take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
-    l.reg_keys = take(pl.P * pl.cap * pl.key_bytes + 64);
-    l.reg_vals = (uint32_t *)take(pl.pairs ? pl.P * pl.cap * 4 : 0);
+    const int64_t region_keys = pl.merge ? pl.n : pl.P * pl.cap;
+    l.reg_keys = take(region_keys * pl.key_bytes + 64);
+    l.reg_vals = (uint32_t *)take(pl.pairs ? region_keys * 4 : 0);
     l.vsize = (uint32_t *)take(pl.P * 4);
     l.voff = (uint64_t *)take((pl.P + 1) * 8);
     l.slow_list = (uint32_t *)take(pl.P * 4);
+    if (pl.merge) {
+        l.rs_phi = (uint32_t *)take(pl.sample_size * 4);
+        l.rs_tag = (uint32_t *)take(pl.sample_size * 4);
+        l.part = (uint32_t *)take((pl.p + 1) * pl.R * 4);
+    } else {
+        l.rs_phi = l.rs_tag = l.part = nullptr;
+    }
     if (pl.classify == BSPS_LEARNED) {
         l.mlp_params = (float *)take(kParams * 4);
         l.mlp_part = (float *)take((int64_t)kMlpGridMax * (kParams + 1) * 4);
@@ -235,11 +264,12 @@ static void to_public(const Plan &p, bsps_plan *out) {
 // slots whose byte position is constant return at once).
 static int kernels_per_call(const Plan &pl) {
     int k = 1;                                   // sample (random draw or block sort)
-    if (run_keys_cluster(pl)) k += 2;            // keys-only and few-values block samplers before the stable one
+    if (run_keys_cluster(pl)) k += pl.merge ? 1 : 2;  // keys-only (and few-values) block samplers before the stable one
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts
     k += 2;                                      // splitters, radix index
+    if (pl.merge) return k + 3;                  // partition, bucket offsets, merge
     k += 2;                                      // routing, bucket offsets
     k += 3;                                      // copy or keys-only tier, cluster sort, out-of-core sort
     if (pl.classify == BSPS_LEARNED) k += mlp_train_kernels();  // training set, start, Adam steps, tables, index
@@ -291,20 +321,36 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     }
     void *const *ev = dbg ? dbg->phase_events : nullptr;
     auto mark = [&](int i) { return ev ? cudaEventRecord((cudaEvent_t)ev[i], c.stream) : cudaSuccess; };
-    if (c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
+    if (c.pl.pairs && !c.pl.merge) BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
     BSPS_CUDA(cudaMemsetAsync(c.ly.cursor, 0, (size_t)c.pl.P * 4, c.stream));
     if (!c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.retry_flag, 0, (size_t)c.pl.P * 4, c.stream));
     BSPS_CUDA(mark(0));
     BSPS_CUDA(launch_sample(c));
+    if (c.pl.merge) {  // every block's own sample records, for the partition (the sample sort reuses the buffer)
+        BSPS_CUDA(cudaMemcpyAsync(c.ly.rs_phi, c.ly.sphi[0], (size_t)c.pl.sample_size * 4, cudaMemcpyDeviceToDevice,
+                                  c.stream));
+        BSPS_CUDA(cudaMemcpyAsync(c.ly.rs_tag, c.ly.stag[0], (size_t)c.pl.sample_size * 4, cudaMemcpyDeviceToDevice,
+                                  c.stream));
+    }
     BSPS_CUDA(mark(1));
     BSPS_CUDA(launch_sample_sort(c));
     BSPS_CUDA(mark(2));
     BSPS_CUDA(launch_splitters(c));
     if (c.pl.classify == BSPS_LEARNED) BSPS_CUDA(launch_mlp_train(c));
     BSPS_CUDA(mark(3));
-    BSPS_CUDA(launch_route(c));
-    BSPS_CUDA(mark(4));
-    BSPS_CUDA(launch_bucket_sort(c));
+    if (c.pl.merge) {
+        BSPS_CUDA(launch_merge_partition(c));
+        BSPS_CUDA(launch_bucket_finish(c));
+        BSPS_CUDA(mark(4));
+        BSPS_CUDA(launch_merge_buckets(c));
+        if (dbg && dbg->partition)
+            BSPS_CUDA(cudaMemcpyAsync(dbg->partition, c.ly.part, (size_t)(c.pl.p + 1) * c.pl.R * 4,
+                                      cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+        BSPS_CUDA(launch_route(c));
+        BSPS_CUDA(mark(4));
+        BSPS_CUDA(launch_bucket_sort(c));
+    }
     BSPS_CUDA(mark(5));
     if (dbg) BSPS_CUDA(launch_debug(c));
     if (dbg && dbg->launches) *dbg->launches = kernels_per_call(c.pl) + debug_kernels(c);

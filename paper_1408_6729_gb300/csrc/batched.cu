@@ -209,6 +209,8 @@ static int make_batch_plan(const int64_t *h_off, int32_t num, int32_t dtype, con
     if (num < 0 || (num > 0 && !h_off) || !prm || !valid_tune(t)) return BSPS_ERR_INVALID_ARG;
     if (dtype < BSPS_U32 || dtype > BSPS_F64) return BSPS_ERR_UNSUPPORTED_DTYPE;
     if (num > 0 && h_off[0] != 0) return BSPS_ERR_INVALID_ARG;
+    // the on-chip instances run the bucket-sort path with the tie-break
+    if (prm->final_step != BSPS_FINAL_SORT || prm->duplicates != BSPS_DUP_TAGS) return BSPS_ERR_INVALID_ARG;
     bp.inst.resize(num);
     bp.bbase.assign(num + 1, 0);
     bp.jobs.clear();

@@ -54,6 +54,8 @@ template <typename K> struct LsdBuffers {
 struct Plan {
     int64_t n, p, R, s, m, M, x, q, sample_size;
     int sampling, dtype, pairs, classify;
+    int dup_off;       // keys compared by value alone (no tie-break by position)
+    int merge;         // final step: merge of the sorted blocks' segments (Fig. 1 step 12)
     uint64_t seed;
     int64_t B;         // refine: sub-buckets per bucket
     int64_t P;         // vbuckets = p * B
@@ -92,7 +94,7 @@ struct Layout {
     float *mlp_x, *mlp_y;                // training points
     int64_t *mlp_npts;
     struct MlpNorm *mlp_norm;
-    void *mlp_opt;                       // Adam state
+    void *mlp_opt;                       // gradient-descent state
     struct MlpTables *mlp_tables;        // the trained network's evaluation form
     float *mlp_ysplit;                   // the network's output for every splitter
     uint16_t *ylut;                      // index over the network's output (kYCells + 1)
@@ -101,6 +103,9 @@ struct Layout {
     uint32_t *vsize;        // P sub-bucket sizes
     uint64_t *voff;         // P + 1 exclusive offsets
     uint32_t *slow_list;    // sub-buckets too large for the on-chip sort
+    // merge final step (merge == 1); reg_keys / reg_vals then hold the sorted blocks
+    uint32_t *rs_phi, *rs_tag;  // R * s: every block's own sample records, before the sample sort
+    uint32_t *part;             // (p + 1) * R: c[k][i] at i * R + k
 };
 
 struct Ctx {
@@ -124,6 +129,7 @@ cudaError_t launch_sample(const Ctx &c);          // Fig. 1 steps 3-4 / Fig. 3 s
 cudaError_t launch_sample_sort(const Ctx &c);     // Fig. 1 step 5
 cudaError_t launch_splitters(const Ctx &c);       // Fig. 1 steps 6-7
 cudaError_t launch_route(const Ctx &c);           // Fig. 1 steps 9-11
+cudaError_t launch_bucket_finish(const Ctx &c);   // sizes in cursor -> offsets, bucket sizes, statistics
 cudaError_t launch_bucket_sort(const Ctx &c);     // Fig. 2 step 12
 cudaError_t launch_debug(const Ctx &c);           // optional diagnostics
 cudaError_t launch_mlp_train(const Ctx &c);       // learned classifier: training set, spline start, training,
@@ -133,9 +139,15 @@ size_t mlp_opt_bytes();
 
 // Byte counts of dynamic shared memory (host side).
 size_t route_smem_bytes(const Plan &pl);
-bool msd_sample_sort(const Plan &p);
-int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)               // MSD sample sort is launched (32-bit keys, large samples)
+bool msd_sample_sort(const Plan &p);                // MSD sample sort is launched (32-bit keys, large samples)
+int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
+// merge final step (Fig. 1 steps 9-12)
+cudaError_t launch_merge_partition(const Ctx &c); // c[k][i] and the bucket sizes (into cursor)
+cudaError_t launch_merge_buckets(const Ctx &c);   // gather + stable merge per bucket
+int merge_cluster(const Plan &pl);                // CTAs per bucket for a bound pl.cap (0: too large)
+int64_t merge_capacity(int cl);                   // keys a cluster of cl CTAs merges
+int64_t merge_runs_max();                         // largest R
 size_t route_keys_smem_bytes(const Plan &pl);
 bool route_keys_splitters_in_smem(const Plan &pl);  // keys-only routing holds the splitters on chip
 

@@ -43,6 +43,7 @@ template <typename K> struct RouteArgs {
     const uint16_t *ylut;         // ... and the index over its output
     int64_t stall_tile;          // test hook: tile stall_tile - 1 never publishes (0: none)
     uint32_t spin_limit;         // polls of one bounded wait
+    uint32_t tag_floor;          // a key's tag is max(position, tag_floor): n - 1 drops the tie-break
 };
 
 template <typename K> struct RouteFixed {
@@ -161,13 +162,15 @@ __global__ void __launch_bounds__(kRouteThreads, 1) route_kernel(const RouteArgs
                     if (ok) {
                         uint32_t steps;
                         bool mis;
-                        b = classify_learned<DT>(kk[i], (uint32_t)(t0 + e), *mt, lut, nsplit, sphi, stag, steps,
-                                                 mis);
+                        b = classify_learned<DT>(kk[i], max((uint32_t)(t0 + e), a.tag_floor), *mt, lut, nsplit,
+                                                 sphi, stag, steps, mis);
                         n_mis += mis;
                         n_steps += steps;
                     }
                 } else {
-                    if (ok) b = classify_key(KeyTraits<DT>::phi(kk[i]), (uint32_t)(t0 + e), lp, lut, sphi, stag);
+                    if (ok)
+                        b = classify_key(KeyTraits<DT>::phi(kk[i]), max((uint32_t)(t0 + e), a.tag_floor), lp, lut,
+                                         sphi, stag);
                 }
                 // keys of lane 0's bucket are counted with one atomic (runs
                 // of equal buckets are common in skewed inputs)
@@ -416,6 +419,7 @@ template <int DT, bool LEARNED> static cudaError_t launch_route_t(const Ctx &c) 
     a.ylut = c.ly.ylut;
     a.stall_tile = c.dbg.stall_tile;
     a.spin_limit = c.dbg.wait_polls ? c.dbg.wait_polls : kSpinLimit;
+    a.tag_floor = c.pl.dup_off ? (uint32_t)(c.pl.n - 1) : 0u;
     const size_t smem = RouteSmemLayout<K, LEARNED>((uint32_t)p.P).total;
     auto kern = route_kernel<DT, LEARNED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -445,6 +449,11 @@ static cudaError_t launch_route_pairs(const Ctx &c) {
 cudaError_t launch_route(const Ctx &c) {
     cudaError_t e = c.pl.pairs ? launch_route_pairs(c) : launch_route_keys(c);
     if (e != cudaSuccess) return e;
+    return launch_bucket_finish(c);
+}
+
+// sub-bucket sizes (in cursor) -> sizes, output offsets, bucket sizes, maxima
+cudaError_t launch_bucket_finish(const Ctx &c) {
     const Plan &p = c.pl;
     bucket_finish_kernel<<<1, 1024, 0, c.stream>>>(c.ly.cursor, (uint32_t)p.P, p.B, p.cap, c.ly.vsize, c.ly.voff,
                                                    c.bucket_sizes, c.ly.status);

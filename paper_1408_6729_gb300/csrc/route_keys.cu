@@ -41,6 +41,7 @@ template <typename K> struct RouteKeysArgs {
     DevStatus *st;
     const MlpTables *mlp_tables;  // learned classifier (nullable): the network's evaluation form
     const uint16_t *ylut;         // ... and the index over its output
+    uint32_t tag_floor;           // a key's tag is max(position, tag_floor): n - 1 drops the tie-break
 };
 
 // Shared memory: the radix index (with the learned classifier: the index over
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kRkThreads, 1) route_keys_kernel(const RouteKe
             kk[i] = ph;
             uint32_t b = P;
             if (ok) {
-                const uint32_t g = (uint32_t)(e0 + q);  // tag: input position
+                const uint32_t g = max((uint32_t)(e0 + q), a.tag_floor);  // tag: input position
                 if constexpr (LEARNED) {
                     uint32_t steps;
                     bool mis;
@@ -308,6 +309,7 @@ template <int DT, bool LEARNED> static cudaError_t launch_t(const Ctx &c) {
     a.st = c.ly.status;
     a.mlp_tables = c.ly.mlp_tables;
     a.ylut = c.ly.ylut;
+    a.tag_floor = c.pl.dup_off ? (uint32_t)(c.pl.n - 1) : 0u;
     if (a.chunks == 0) return cudaSuccess;
     const size_t smem = RouteKeysLayout<K, LEARNED>((uint32_t)p.P).total;
     auto kern = route_keys_kernel<DT, LEARNED>;

@@ -35,13 +35,16 @@ __global__ void sample_random_kernel(const typename KeyTraits<DT>::T *__restrict
 // Regular oversampling (Fig. 1 steps 3-4): one cluster of CL CTAs sorts the
 // block of virtual processor k stably and emits the records at sorted
 // positions j*x - 1, j = 1..s.  Positions at or past the block's key count are
-// pads (Lemma 5.1's padding), which follow every key in tag order.
+// pads (Lemma 5.1's padding), which follow every key in tag order.  For the
+// merge final step (Fig. 1 step 12) the sorted block itself is written too
+// (`runs`, with its payloads), at the block's place.
 // ---------------------------------------------------------------------------
 template <int DT, int CL, int ITEMS>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSortThreads, 1)
 run_sample_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m,
                   int64_t M, int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag,
-                  uint32_t *too_big, const uint32_t *only) {
+                  uint32_t *too_big, const uint32_t *only, typename KeyTraits<DT>::T *runs,
+                  const uint32_t *__restrict__ vals, uint32_t *runs_val) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSort<K, true, CL, ITEMS>;
     if (only && only[blockIdx.x / CL] == 0) return;  // only the blocks the keys-only sort gave back
@@ -65,6 +68,10 @@ run_sample_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n,
     if (len == 0) return;
     auto load = [&](int64_t e) { return KeyTraits<DT>::phi(keys[lo + e]); };
     auto emit = [&](uint32_t pos, K key, uint32_t slot) {
+        if (runs) {  // the sorted block is kept for the merge final step
+            runs[lo + pos] = key;
+            if (runs_val) runs_val[lo + pos] = vals[lo + slot];
+        }
         if ((pos + 1) % x == 0) {
             const int64_t j = (pos + 1) / x;
             sphi[k * s + (j - 1)] = key;
@@ -83,7 +90,8 @@ constexpr int kRunKeysItems = 20;  // 512 threads x 20 = 10240 keys per CTA (roo
 template <int DT, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 1)
 run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t M,
-                       int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry) {
+                       int64_t s, int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry,
+                       typename KeyTraits<DT>::T *runs, const uint32_t *__restrict__ vals, uint32_t *runs_val) {
     using K = typename KeyTraits<DT>::T;
     static_assert(sizeof(K) == 4, "32-bit keys and 32-bit positions in one word");
     using SS = SegSortKeys<uint64_t, CL, kRunKeysItems>;
@@ -131,6 +139,10 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
     };
     const uint32_t xx = (uint32_t)x;
     auto emit = [&](uint32_t pos, uint64_t key) {
+        if (runs) {  // the sorted block is kept for the merge final step
+            runs[lo + pos] = (K)(key >> 32);
+            if (runs_val) runs_val[lo + pos] = vals[lo + (uint32_t)key];
+        }
         if ((pos + 1) % xx == 0) {
             const int64_t j = (pos + 1) / xx;
             sphi[k * s + (j - 1)] = (K)(key >> 32);
@@ -926,7 +938,7 @@ __global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits
                                  const typename KeyTraits<DT>::T *vphi, const uint32_t *vtag,
                                  const uint16_t *lut,
                                  const LutParams<typename KeyTraits<DT>::T> *lutp, const MlpTables *mlp_tables,
-                                 const uint16_t *ylut, int64_t P, int32_t *out) {
+                                 const uint16_t *ylut, int64_t P, uint32_t tag_floor, int32_t *out) {
     __shared__ __align__(16) unsigned char mt_raw[LEARNED ? sizeof(MlpTables) : 16];
     const MlpTables *mt = reinterpret_cast<const MlpTables *>(mt_raw);
     if constexpr (LEARNED) {
@@ -941,10 +953,11 @@ __global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits
     if constexpr (LEARNED) {
         uint32_t steps;
         bool mis;
-        v = classify_learned<DT>(keys[g], (uint32_t)g, *mt, ylut, (uint32_t)(P - 1), vphi, vtag, steps, mis);
+        v = classify_learned<DT>(keys[g], max((uint32_t)g, tag_floor), *mt, ylut, (uint32_t)(P - 1), vphi, vtag,
+                                 steps, mis);
     } else {
         const LutParams<typename KeyTraits<DT>::T> lp = *lutp;
-        v = classify_key(KeyTraits<DT>::phi(keys[g]), (uint32_t)g, lp, lut, vphi, vtag);
+        v = classify_key(KeyTraits<DT>::phi(keys[g]), max((uint32_t)g, tag_floor), lp, lut, vphi, vtag);
     }
     out[g] = (int32_t)(v / B);
 }
@@ -952,14 +965,16 @@ __global__ void __launch_bounds__(256) bucket_of_kernel(const typename KeyTraits
 template <typename K>
 __global__ void pad_sizes_kernel(int64_t n, int64_t R, int64_t m, int64_t M, int64_t B, const K *vphi,
                                  const uint32_t *vtag, const uint16_t *lut, const LutParams<K> *lutp,
-                                 unsigned long long *out) {
+                                 int dup_off, unsigned long long *out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= R * M) return;
     const int64_t k = t / M, j = t % M;
     const int64_t len = k * m < n ? min(m, n - k * m) : 0;
     if (j < len) return;
     const LutParams<K> lp = *lutp;
-    const uint32_t v = classify_key(all_ones<K>(), (uint32_t)(n + k * M + j), lp, lut, vphi, vtag);
+    // without tags a pad equals the pad splitters and follows them all
+    const uint32_t tag = dup_off ? 0xffffffffu : (uint32_t)(n + k * M + j);
+    const uint32_t v = classify_key(all_ones<K>(), tag, lp, lut, vphi, vtag);
     atomicAdd(&out[v / B], 1ull);
 }
 
@@ -986,7 +1001,8 @@ template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const 
     const Plan &p = c.pl;
     kern<<<(unsigned)(p.R * CL), kSortThreads, smem, c.stream>>>(
         (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0],
-        (uint32_t *)&c.ly.status->run_too_big, only);
+        (uint32_t *)&c.ly.status->run_too_big, only, p.merge ? (K *)c.ly.reg_keys : nullptr, c.vals_in,
+        p.merge && p.pairs ? c.ly.reg_vals : nullptr);
     return cudaGetLastError();
 }
 
@@ -1000,8 +1016,9 @@ template <int DT, int CL> static cudaError_t launch_run_sample_keys(const Ctx &c
     const Plan &p = c.pl;
     e = cudaMemsetAsync(c.ly.run_retry, 0, (size_t)p.R * 4, c.stream);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(p.R * CL), 512, smem, c.stream>>>((const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x,
-                                                        (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
+    kern<<<(unsigned)(p.R * CL), 512, smem, c.stream>>>(
+        (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry,
+        p.merge ? (K *)c.ly.reg_keys : nullptr, c.vals_in, p.merge && p.pairs ? c.ly.reg_vals : nullptr);
     return cudaGetLastError();
 }
 
@@ -1034,7 +1051,7 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
         default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
         }
         if (e != cudaSuccess) return e;
-        if (only) {  // blocks of few distinct keys, before the stable sort
+        if (only && !p.merge) {  // blocks of few distinct keys, before the stable sort (it keeps no sorted block)
             e = cudaFuncSetAttribute(run_sample_lowcard_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kLowCardSmem);
             if (e != cudaSuccess) return e;
@@ -1167,7 +1184,8 @@ template <int DT> static cudaError_t launch_debug_t(const Ctx &c) {
         auto kern = p.classify == BSPS_LEARNED ? bucket_of_kernel<DT, true> : bucket_of_kernel<DT, false>;
         kern<<<(unsigned)((p.n + 255) / 256), 256, 0, c.stream>>>(
             (const K *)c.keys_in, p.n, p.B, (const K *)c.ly.vphi, c.ly.vtag, c.ly.lut,
-            (const LutParams<K> *)c.ly.lutp, c.ly.mlp_tables, c.ly.ylut, p.P, c.dbg.bucket_of);
+            (const LutParams<K> *)c.ly.lutp, c.ly.mlp_tables, c.ly.ylut, p.P,
+            p.dup_off ? (uint32_t)(p.n - 1) : 0u, c.dbg.bucket_of);
     }
     if (c.dbg.pad_sizes) {
         cudaError_t e = cudaMemsetAsync(c.dbg.pad_sizes, 0, sizeof(int64_t) * p.p, c.stream);
@@ -1175,7 +1193,7 @@ template <int DT> static cudaError_t launch_debug_t(const Ctx &c) {
         if (regular && p.R * p.M > p.n)
             pad_sizes_kernel<K><<<(unsigned)((p.R * p.M + 255) / 256), 256, 0, c.stream>>>(
                 p.n, p.R, p.m, p.M, p.B, (const K *)c.ly.vphi, c.ly.vtag, c.ly.lut,
-                (const LutParams<K> *)c.ly.lutp, (unsigned long long *)c.dbg.pad_sizes);
+                (const LutParams<K> *)c.ly.lutp, p.dup_off, (unsigned long long *)c.dbg.pad_sizes);
     }
     return cudaGetLastError();
 }

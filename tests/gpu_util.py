@@ -34,14 +34,16 @@ class GpuResult:
 
 
 def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_pct=0,
-            debug=True, bucket_of=None, classify=0):
-    """Sort with the library; returns keys, vals, sizes, sample, splitters, bucket_of, pads, stats."""
+            debug=True, bucket_of=None, classify=0, final_step=0, duplicates=0, expect_status=0):
+    """Sort with the library; returns keys, vals, sizes, sample, splitters, bucket_of, pads, stats
+    (and, for the merge final step, the partition as an R x (p+1) array)."""
     import torch
     bsps = lib()
     n = keys.shape[0]
     code = code_of(keys)
     prm = bsps.make_params(p, s=s, runs=runs, sampling=mode, seed=seed, refine=refine,
-                           capacity_pct=capacity_pct, classify=classify)
+                           capacity_pct=capacity_pct, classify=classify, final_step=final_step,
+                           duplicates=duplicates)
     pl = bsps.bsps_get_plan(n, code, prm, vals is not None)
     ws = torch.empty(max(pl.workspace_bytes, 1), dtype=torch.uint8, device="cuda:0")
     kin = to_dev(keys)
@@ -57,11 +59,14 @@ def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_
     pads = torch.full((p,), -1, dtype=torch.int64, device="cuda:0") if debug else None
     mlp_params = torch.zeros(bsps.MLP_PARAMS, dtype=torch.float32, device="cuda:0") if classify else None
     mlp_loss = torch.zeros(2, dtype=torch.float32, device="cuda:0") if classify else None
+    part = torch.full(((p + 1) * pl.R,), -1, dtype=torch.int32, device="cuda:0") \
+        if (debug and final_step and n > 0) else None
     rc = bsps.bsps_sort_debug(kin, vin, kout, vout, n, code, prm, sizes, ws, sample=sample,
                               splitters=spl, bucket_of=bo, pad_sizes=pads, mlp_params=mlp_params,
-                              mlp_loss=mlp_loss)
+                              mlp_loss=mlp_loss, partition=part)
     assert rc == 0, bsps.bsps_strerror(rc)
     st = bsps.bsps_read_stats(ws)
+    assert st.status == expect_status, (st.status, bsps.bsps_strerror(st.status))
     r = GpuResult()
     r.plan = pl
     r.stats = st
@@ -74,6 +79,8 @@ def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_
     r.pad_sizes = pads.cpu().numpy() if debug else None
     r.mlp_params = mlp_params.cpu().numpy() if classify else None
     r.mlp_loss = mlp_loss.cpu().numpy() if classify else None
+    r.partition = part.cpu().numpy().view(np.uint32).reshape(p + 1, pl.R).T.astype(np.int64) \
+        if part is not None else None
     return r
 
 

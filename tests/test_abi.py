@@ -71,3 +71,29 @@ def test_host_side_argument_errors(lib):
     rc = lib.load().bsps_sort_keys(8, 8, 10, lib.BSPS_I32, prm, None, 256, 1 << 40, None)
     assert rc == lib.BSPS_ERR_INVALID_ARG          # in place
     assert lib.bsps_strerror(lib.BSPS_ERR_BUCKET_OVERFLOW)
+
+
+def test_merge_final_step_and_duplicate_switch_arguments(lib):
+    """The merge final step ends Sort_Det_BSP (Fig. 1 step 12): regular
+    sampling, 4-byte keys, tree classification, no sub-buckets, at most 8192
+    blocks, and a bucket bound of Lemma 5.1 one cluster can merge."""
+    M = lib.BSPS_FINAL_MERGE
+    for kw in (dict(sampling=lib.BSPS_RANDOM), dict(refine=2), dict(classify=lib.BSPS_LEARNED),
+               dict(runs=16384)):
+        with pytest.raises(ValueError, match="invalid"):
+            lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64, final_step=M, **kw))
+    with pytest.raises(ValueError, match="invalid"):
+        lib.bsps_get_plan(1 << 20, lib.BSPS_F64, lib.make_params(64, final_step=M))
+    for kw in (dict(final_step=2), dict(duplicates=2)):
+        with pytest.raises(ValueError, match="invalid"):
+            lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64, **kw))
+    # config 1 with s = 8: the bound (145,347 keys) exceeds a cluster's 131,072
+    with pytest.raises(ValueError, match="too large"):
+        lib.bsps_get_plan(1 << 20, lib.BSPS_U32, lib.make_params(64, s=8, final_step=M))
+    # the regular headline shape: eight CTAs per bucket, no bucket regions
+    pl = lib.bsps_get_plan(1 << 28, lib.BSPS_I32, lib.make_params(4096, s=4096, final_step=M))
+    assert pl.bucket_cluster == 8 and pl.refine == 1 and pl.capacity == 131072
+    plain = lib.bsps_get_plan(1 << 28, lib.BSPS_I32, lib.make_params(4096, s=4096))
+    assert pl.workspace_bytes < plain.workspace_bytes
+    dup = lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64, duplicates=lib.BSPS_DUP_OFF))
+    assert dup.workspace_bytes == lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64)).workspace_bytes

@@ -152,7 +152,7 @@ def test_out_of_core_bucket_path(pairs):
 
 def test_overflow_is_reported_not_written():
     keys = gen.uniform(200_000, 16, 2)
-    gpu = run_gpu(keys, 16, 0, 0, oracle.RANDOM, 3, capacity_pct=60, debug=False)
+    gpu = run_gpu(keys, 16, 0, 0, oracle.RANDOM, 3, capacity_pct=60, debug=False, expect_status=-4)
     assert gpu.stats.overflow == 1
     assert gpu.stats.status == -4  # BSPS_ERR_BUCKET_OVERFLOW
 
