@@ -94,7 +94,7 @@ typedef enum { BSPS_DUP_TAGS = 0, BSPS_DUP_OFF = 1 } bsps_duplicates;
  *             BSPS_FINAL_SORT.  It requires regular sampling, 4-byte keys,
  *             R <= 8192, refine 0 or 1 and tree classification
  *             (BSPS_ERR_INVALID_ARG otherwise), and a bucket bound of Lemma
- *             5.1 of at most 131,072 keys (BSPS_ERR_TOO_LARGE otherwise).
+ *             5.1 of at most 126,976 keys (BSPS_ERR_TOO_LARGE otherwise).
  *   duplicates  bsps_duplicates.  BSPS_DUP_OFF compares keys by value
  *             alone: a key goes to bucket #{i : phi(S_i) <= phi(key)}, every
  *             key equal to a splitter in the highest such bucket.  It is the

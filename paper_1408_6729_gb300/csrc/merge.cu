@@ -13,7 +13,7 @@
 namespace bsps {
 
 constexpr int kMergeThreads = 512;
-constexpr int kMergeItems = 32;                             // outputs per thread per merge round
+constexpr int kMergeItems = 31;                             // outputs per thread per merge round (at most)
 constexpr int kMergeCap = kMergeThreads * kMergeItems;     // keys one CTA holds
 constexpr int kMergeRunsMax = 8192;                         // blocks R (segment offsets in shared memory)
 constexpr int kPartWarps = 16;
@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(kMergeThreads, PAIRS ? 1 : 2) merge_bucket_ker
     if (tid == 0) soff[R] = N;
     __syncthreads();
     const uint32_t P0 = Pb[c], P1 = Pb[c + 1], cnt = P1 - P0;
-    const uint32_t E = (cnt + kMergeThreads - 1) / kMergeThreads;
+    // consecutive outputs per thread, odd: lane t's e-th item sits at t*E + e,
+    // so the 32 lanes of a warp touch 32 different shared-memory banks
+    const uint32_t E = ((cnt + kMergeThreads - 1) / kMergeThreads) | 1u;
     const uint32_t o0 = min(cnt, tid * E), o1 = min(cnt, o0 + E);
     // the segment holding bucket position q: the last k with soff[k] <= q
     auto seg_of = [&](uint32_t q) {

@@ -87,12 +87,12 @@ def test_merge_final_step_and_duplicate_switch_arguments(lib):
     for kw in (dict(final_step=2), dict(duplicates=2)):
         with pytest.raises(ValueError, match="invalid"):
             lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64, **kw))
-    # config 1 with s = 8: the bound (145,347 keys) exceeds a cluster's 131,072
+    # config 1 with s = 8: the bound (145,347 keys) exceeds a cluster's 126,976
     with pytest.raises(ValueError, match="too large"):
         lib.bsps_get_plan(1 << 20, lib.BSPS_U32, lib.make_params(64, s=8, final_step=M))
     # the regular headline shape: eight CTAs per bucket, no bucket regions
     pl = lib.bsps_get_plan(1 << 28, lib.BSPS_I32, lib.make_params(4096, s=4096, final_step=M))
-    assert pl.bucket_cluster == 8 and pl.refine == 1 and pl.capacity == 131072
+    assert pl.bucket_cluster == 8 and pl.refine == 1 and pl.capacity == 126976
     plain = lib.bsps_get_plan(1 << 28, lib.BSPS_I32, lib.make_params(4096, s=4096))
     assert pl.workspace_bytes < plain.workspace_bytes
     dup = lib.bsps_get_plan(1 << 20, lib.BSPS_I32, lib.make_params(64, duplicates=lib.BSPS_DUP_OFF))

@@ -32,8 +32,8 @@ def _check_partition(gpu, ref, n):
 MERGE_CASES = [
     ("u32_p16_cl1", lambda: gen.uniform_u32(1 << 16, seed=3), 16, 64, 16),
     ("i32_p64_s512_cl2", lambda: gen.uniform(1 << 20, 64, 1), 64, 512, 0),
-    ("i32_p64_cl4", lambda: gen.uniform(1 << 21, 64, 2), 64, 64, 0),
-    ("i32_p64_cl8", lambda: gen.uniform(1 << 22, 64, 3), 64, 64, 0),
+    ("i32_p64_cl4", lambda: gen.uniform(1 << 21, 64, 2), 64, 128, 0),
+    ("i32_p64_cl8", lambda: gen.uniform(1 << 22, 64, 3), 64, 128, 0),
     ("zipf_p256_R512", lambda: gen.zipf(1 << 21, seed=4), 256, 256, 512),
     ("f32_gmm_ragged", lambda: gen.gmm(1_000_003, seed=5).astype(np.float32), 128, 256, 0),
     ("zero_entropy", lambda: gen.zero_entropy(300_007), 32, 64, 0),
