@@ -49,6 +49,11 @@ WORKLOADS = {
     "zipf_2e28_int32_pairs_p4096_regular_merge": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096,
                                                      pairs=True, final_step=1, compare="sort",
                                                      make=lambda n, p, seed: gen.zipf(n, seed=seed)),
+    # the merge's kernels on a quarter of the data (16-key segments as at 2^28),
+    # for full ncu captures
+    "uniform_2e26_int32_p2048_regular_merge": dict(n=1 << 26, p=2048, sampling=0, s=2048, runs=2048,
+                                                  pairs=False, final_step=1,
+                                                  make=lambda n, p, seed: gen.uniform(n, p, seed)),
     # the cost of the duplicate handling (Sec. 6.4 measures it): the headline
     # sort without the tie-break, and with it (timed beside) on the same keys
     "uniform_2e28_int32_p4096_random_nodup": dict(n=1 << 28, p=4096, sampling=1, s=0, runs=0, pairs=False,
@@ -408,7 +413,7 @@ def run_gpu(args, wl, name):
                     "oracle_s": round(time.perf_counter() - t0, 1)}
         del ref
     compare = None
-    if wl.get("compare"):
+    if wl.get("compare") and not args.no_compare:
         compare = compare_variant(args, bsps, kin, vin, kout, vout, sizes, n, code, wl, rank, st, stream,
                                   elapsed_ms)
 
@@ -781,6 +786,7 @@ def main():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg (profiling runs)")
     ap.add_argument("--refine", type=int, default=0, help="sub-buckets per bucket (0: the library's choice)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the variant timed beside (profiling runs)")
     ap.add_argument("--no-verify", action="store_true",
                     help="skip the oracle comparison of the last output (profiling runs)")
     args = ap.parse_args()

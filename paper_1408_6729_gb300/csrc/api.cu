@@ -272,6 +272,9 @@ static int kernels_per_call(const Plan &pl) {
     if (pl.merge) return k + 3;                  // partition, bucket offsets, merge
     k += 2;                                      // routing, bucket offsets
     k += 3;                                      // copy or keys-only tier, cluster sort, out-of-core sort
+    if (!pl.pairs && pl.key_bytes == 8 && pl.bucket_cl * 512 * kKeysItems64 < 8 * 512 * kKeysItems64Large &&
+        pl.cap > (int64_t)pl.bucket_cl * 512 * kKeysItems64)
+        k += 1;                                  // the larger keys-only tier
     if (pl.classify == BSPS_LEARNED) k += mlp_train_kernels();  // training set, start, Adam steps, tables, index
     return k;
 }

@@ -3,8 +3,10 @@
 // to the bucket's place in the output.  Each sub-bucket is sorted on chip by
 // one thread-block cluster, in up to three tiers:
 //   1. keys only: the throughput sort of segsort_keys.cuh (unstable ranks,
-//      which equal keys cannot reveal); with payloads: sub-buckets of one key
-//      value are copied as they stand;
+//      which equal keys cannot reveal) -- for 8-byte keys in two capacities,
+//      two CTAs per SM for the sub-buckets that fit, then one CTA per SM
+//      holding twice the keys for the larger ones; with payloads: sub-buckets
+//      of one key value are copied as they stand;
 //   2. the other sub-buckets with payloads, or what tier 1 gives back: the
 //      stable cluster sort of segsort.cuh over a list;
 //   3. sub-buckets larger than a cluster's shared memory: an out-of-core
@@ -32,6 +34,8 @@ template <typename K> struct BucketArgs {
     uint32_t *retry_list;
     const uint32_t *only;     // tier 2 over a list (nullable: every sub-bucket)
     const int32_t *only_count;
+    int64_t defer_above;      // tier 1: sub-buckets above this many keys are left to the larger tier 1
+    int64_t take_above;       // larger tier 1: only sub-buckets above this many keys
 };
 
 template <int DT, bool PAIRS, int CL, int ITEMS>
@@ -103,14 +107,14 @@ __global__ void __launch_bounds__(kCopyThreads) bucket_copy_kernel(const BucketA
 // Tier 1 (keys only): one cluster per sub-bucket; its bounds are the two
 // splitters around it (the smallest and largest key for the end buckets).
 template <int DT, int CL, int ITEMS>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, ITEMS > kKeysItems64 ? 1 : 2)
 bucket_keys_kernel(const BucketArgs<typename KeyTraits<DT>::T> a) {
     using K = typename KeyTraits<DT>::T;
     using SS = SegSortKeys<K, CL, ITEMS, false>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t v = blockIdx.x / CL;
     const int64_t cnt = imin64(a.vsize[v], a.cap);
-    if (cnt == 0) return;
+    if (cnt == 0 || cnt > a.defer_above || cnt <= a.take_above) return;
     const K lo = v > 0 ? a.vphi[v - 1] : (K)~a.st->ext_min_inv;
     const K hi = v < a.P - 1 ? a.vphi[v] : (K)a.st->ext_max;
     K *out_k = a.out_keys + a.voff[v];
@@ -298,8 +302,10 @@ static cudaError_t launch_keys(const Ctx &c, const BucketArgs<typename KeyTraits
         return cudaGetLastError();
     } else {
         using SS = SegSortKeys<K, CL, ITEMS, false>;
-        // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
-        static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024, "two CTAs per SM");
+        // two CTAs per SM (228 KB of shared memory per SM, 1 KB of it reserved
+        // per CTA), or one for the larger tier
+        static_assert(2 * (SS::smem_bytes() + 1024) <= 228 * 1024 || ITEMS > kKeysItems64, "two CTAs per SM");
+        static_assert(SS::smem_bytes() + 1024 <= 228 * 1024, "one CTA per SM");
         const size_t smem = SS::smem_bytes();
         auto kern = bucket_keys_kernel<DT, CL, ITEMS>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -327,11 +333,27 @@ template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
     a.retry_list = c.ly.retry_list;
     a.only = nullptr;
     a.only_count = nullptr;
+    a.defer_above = INT64_MAX;
+    a.take_above = 0;
     constexpr int IT = PAIRS ? (sizeof(K) == 8 ? kPairItems64 : kPairItems32)
                              : (sizeof(K) == 8 ? kBucketItems64 : kBucketItems32);
     cudaError_t e = cudaSuccess;
     if constexpr (!PAIRS) {
         constexpr int KIT = sizeof(K) == 8 ? kKeysItems64 : kKeysItems32;
+        if constexpr (sizeof(K) == 8) {
+            // sub-buckets beyond the two-per-SM clusters: clusters of 8 CTAs
+            // holding twice the keys each, before anything is given back
+            a.defer_above = (int64_t)c.pl.bucket_cl * 512 * KIT;
+            if (a.defer_above < (int64_t)8 * 512 * kKeysItems64Large && c.pl.cap > a.defer_above) {
+                BucketArgs<K> big = a;
+                big.defer_above = INT64_MAX;
+                big.take_above = a.defer_above;
+                e = launch_keys<DT, 8, kKeysItems64Large>(c, big);
+                if (e != cudaSuccess) return e;
+            } else {
+                a.defer_above = INT64_MAX;
+            }
+        }
         switch (c.pl.bucket_cl) {
         case 1: e = launch_keys<DT, 1, KIT>(c, a); break;
         case 2: e = launch_keys<DT, 2, KIT>(c, a); break;

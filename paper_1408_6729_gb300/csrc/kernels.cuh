@@ -35,6 +35,7 @@ constexpr int kPairItems32 = 12;       // sub-bucket sort with payload slots, 4-
 constexpr int kPairItems64 = 8;        // ... 8-byte keys
 constexpr int kKeysItems32 = 20;       // throughput keys-only sort: 512 threads x 20 = 10240 keys per CTA
 constexpr int kKeysItems64 = 10;       // ... 8-byte keys
+constexpr int kKeysItems64Large = 20;  // ... 8-byte keys, one CTA per SM, for the larger sub-buckets
 constexpr int kSlowThreads = 512;      // out-of-core sort of an oversized sub-bucket
 constexpr int kSlowItems = 8;
 

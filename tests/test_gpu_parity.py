@@ -138,6 +138,19 @@ def test_gmm_f64_random_small_sample():
     assert_same(gpu, ref)
 
 
+@pytest.mark.parametrize("refine", [1, 2, 4])
+def test_f64_sub_buckets_above_the_two_per_sm_clusters(refine):
+    """8-byte keys without payloads, few samples per bucket (s = 16): the
+    sub-buckets spread from far below to far above the two-CTAs-per-SM
+    clusters' 40,960 keys, so the larger keys-only tier (81,920), the stable
+    tier and the out-of-core tier all take some."""
+    n, p = 1 << 22, 64
+    keys = gen.gmm(n, seed=12)
+    ref = ref_sort(keys, p, 16, 0, oracle.RANDOM, 5)
+    gpu = run_gpu(keys, p, 16, 0, oracle.RANDOM, 5, refine=refine)
+    assert_same(gpu, ref)
+
+
 @pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
 def test_out_of_core_bucket_path(pairs):
     """Buckets far larger than one cluster's shared memory."""
