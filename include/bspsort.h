@@ -168,10 +168,12 @@ typedef struct {
  *     about a second).  An expired wait records BSPS_ERR_DEVICE_TIMEOUT,
  *     which bsps_read_stats returns; the call's output is then undefined but
  *     every access stays inside the caller's buffers.
- *   partition: with BSPS_FINAL_MERGE, a DEVICE buffer of (p+1)*R uint32 that
- *     receives the partition of Fig. 1 step 9: entry i*R + k is the number of
- *     keys of sorted block k that precede splitter S_i (pads excluded; row 0
- *     is 0, row p the block's key count). */
+ *   partition: a DEVICE buffer of (p+1)*R uint32 that receives the partition
+ *     of Fig. 1 step 9 when the call keeps the sorted blocks (regular
+ *     sampling of 4-byte keys with the tree classifier and R <= 16384, or
+ *     BSPS_FINAL_MERGE): entry i*R + k is the number of keys of sorted block
+ *     k that precede splitter S_i (pads excluded; row 0 is 0, row p the
+ *     block's key count); untouched otherwise. */
 #define BSPS_PHASES 6
 typedef struct {
     bsps_record *sample;     /* plan.sample_size records, sorted */
@@ -184,7 +186,7 @@ typedef struct {
     float *mlp_loss;         /* learned classifier: training loss before and after */
     int32_t stall_tile;      /* test hook (see above); 0: none */
     uint32_t wait_polls;     /* test hook (see above); 0: the default bound */
-    uint32_t *partition;     /* (p+1)*R entries, BSPS_FINAL_MERGE only */
+    uint32_t *partition;     /* (p+1)*R entries (see above) */
 } bsps_debug;
 
 /*

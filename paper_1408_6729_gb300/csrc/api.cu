@@ -53,6 +53,12 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     if (pl.merge && pl.R > merge_runs_max()) return BSPS_ERR_INVALID_ARG;
     pl.dtype = dtype;
     pl.pairs = pairs;
+    // regular sampling of 4-byte keys routes as the paper does (Fig. 1 steps
+    // 9-11): the sorted blocks are kept, partitioned by the splitters and copied
+    // segment by segment -- no per-key classification
+    pl.seg_route = !pl.merge && prm->sampling == BSPS_REGULAR && dtype != BSPS_F64 && prm->classify == BSPS_TREE &&
+                   pl.R <= kSegRouteRunsMax;
+    pl.keep_runs = pl.merge || pl.seg_route;
     pl.seed = prm->seed;
     pl.key_bytes = dtype == BSPS_F64 ? 8 : 4;
     if (prm->s > ((int64_t)1 << 31) || prm->runs > ((int64_t)1 << 30)) return BSPS_ERR_TOO_LARGE;
@@ -161,21 +167,22 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
     take(pl.P * 4);
     take((kLutCells + 2) * 2);
     take(64);
-    const bool look_back = pairs && !pl.merge;
+    const bool look_back = pairs && !pl.keep_runs;
     take(look_back ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
     take(look_back ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     take(pl.P * 4);
     take(pl.P * 4); take(pl.P * 4);
     take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
-    const int64_t region_keys = pl.merge ? n : pl.P * pl.cap;  // the sorted blocks, or the bucket regions
+    const int64_t region_keys = pl.merge ? 0 : pl.P * pl.cap;  // the merge reads the sorted blocks directly
     take(region_keys * pl.key_bytes + 64);
     take(pairs ? region_keys * 4 : 0);
     take(pl.P * 4);
     take((pl.P + 1) * 8);
     take(pl.P * 4);
-    if (pl.merge) {
+    if (pl.keep_runs) {
+        take(n * pl.key_bytes); take(pairs ? n * 4 : 0);
         take(pl.sample_size * 4); take(pl.sample_size * 4);
-        take((pl.p + 1) * pl.R * 4);
+        take((pl.P + 1) * pl.R * 4);
     }
     if (pl.classify == BSPS_LEARNED) {
         take(kParams * 4);
@@ -210,25 +217,28 @@ static Layout make_layout(const Plan &pl, void *ws) {
     l.vtag = (uint32_t *)take(pl.P * 4);
     l.lut = (uint16_t *)take((kLutCells + 2) * 2);
     l.lutp = take(64);
-    const bool look_back = pl.pairs && !pl.merge;
+    const bool look_back = pl.pairs && !pl.keep_runs;
     l.state = (uint32_t *)take(look_back ? std::max<int64_t>(pl.tiles, 1) * pl.P * 4 : 0);
     l.ids = (uint16_t *)take(look_back ? std::max<int64_t>(pl.tiles, 1) * kRouteTile * 2 : 0);
     l.cursor = (uint32_t *)take(pl.P * 4);
     l.retry_flag = (uint32_t *)take(pl.P * 4);
     l.retry_list = (uint32_t *)take(pl.P * 4);
     l.run_retry = (uint32_t *)take(pl.sampling == BSPS_REGULAR ? pl.R * 4 : 0);
-    const int64_t region_keys = pl.merge ? pl.n : pl.P * pl.cap;
+    const int64_t region_keys = pl.merge ? 0 : pl.P * pl.cap;
     l.reg_keys = take(region_keys * pl.key_bytes + 64);
     l.reg_vals = (uint32_t *)take(pl.pairs ? region_keys * 4 : 0);
     l.vsize = (uint32_t *)take(pl.P * 4);
     l.voff = (uint64_t *)take((pl.P + 1) * 8);
     l.slow_list = (uint32_t *)take(pl.P * 4);
-    if (pl.merge) {
+    if (pl.keep_runs) {
+        l.runs = take(pl.n * pl.key_bytes);
+        l.runs_val = (uint32_t *)take(pl.pairs ? pl.n * 4 : 0);
         l.rs_phi = (uint32_t *)take(pl.sample_size * 4);
         l.rs_tag = (uint32_t *)take(pl.sample_size * 4);
-        l.part = (uint32_t *)take((pl.p + 1) * pl.R * 4);
+        l.part = (uint32_t *)take((pl.P + 1) * pl.R * 4);
     } else {
-        l.rs_phi = l.rs_tag = l.part = nullptr;
+        l.runs = nullptr;
+        l.runs_val = l.rs_phi = l.rs_tag = l.part = nullptr;
     }
     if (pl.classify == BSPS_LEARNED) {
         l.mlp_params = (float *)take(kParams * 4);
@@ -264,13 +274,14 @@ static void to_public(const Plan &p, bsps_plan *out) {
 // slots whose byte position is constant return at once).
 static int kernels_per_call(const Plan &pl) {
     int k = 1;                                   // sample (random draw or block sort)
-    if (run_keys_cluster(pl)) k += pl.merge ? 1 : 2;  // keys-only (and few-values) block samplers before the stable one
+    if (run_keys_cluster(pl)) k += 2;            // keys-only and few-values block samplers before the stable one
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts
     k += 2;                                      // splitters, radix index
     if (pl.merge) return k + 3;                  // partition, bucket offsets, merge
-    k += 2;                                      // routing, bucket offsets
+    k += 2;                                      // routing (partition and segment copy: one more), bucket offsets
+    if (pl.seg_route) k += 1;
     k += 3;                                      // copy or keys-only tier, cluster sort, out-of-core sort
     if (!pl.pairs && pl.key_bytes == 8 && pl.bucket_cl * 512 * kKeysItems64 < 8 * 512 * kKeysItems64Large &&
         pl.cap > (int64_t)pl.bucket_cl * 512 * kKeysItems64)
@@ -324,12 +335,13 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     }
     void *const *ev = dbg ? dbg->phase_events : nullptr;
     auto mark = [&](int i) { return ev ? cudaEventRecord((cudaEvent_t)ev[i], c.stream) : cudaSuccess; };
-    if (c.pl.pairs && !c.pl.merge) BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
+    if (c.pl.pairs && !c.pl.keep_runs)
+        BSPS_CUDA(cudaMemsetAsync(c.ly.state, 0, (size_t)c.pl.tiles * c.pl.P * 4, c.stream));
     BSPS_CUDA(cudaMemsetAsync(c.ly.cursor, 0, (size_t)c.pl.P * 4, c.stream));
     if (!c.pl.pairs) BSPS_CUDA(cudaMemsetAsync(c.ly.retry_flag, 0, (size_t)c.pl.P * 4, c.stream));
     BSPS_CUDA(mark(0));
     BSPS_CUDA(launch_sample(c));
-    if (c.pl.merge) {  // every block's own sample records, for the partition (the sample sort reuses the buffer)
+    if (c.pl.keep_runs) {  // every block's own sample records, for the partition (the sample sort reuses the buffer)
         BSPS_CUDA(cudaMemcpyAsync(c.ly.rs_phi, c.ly.sphi[0], (size_t)c.pl.sample_size * 4, cudaMemcpyDeviceToDevice,
                                   c.stream));
         BSPS_CUDA(cudaMemcpyAsync(c.ly.rs_tag, c.ly.stag[0], (size_t)c.pl.sample_size * 4, cudaMemcpyDeviceToDevice,
@@ -341,14 +353,21 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     BSPS_CUDA(launch_splitters(c));
     if (c.pl.classify == BSPS_LEARNED) BSPS_CUDA(launch_mlp_train(c));
     BSPS_CUDA(mark(3));
-    if (c.pl.merge) {
+    if (c.pl.keep_runs) {
         BSPS_CUDA(launch_merge_partition(c));
         BSPS_CUDA(launch_bucket_finish(c));
-        BSPS_CUDA(mark(4));
-        BSPS_CUDA(launch_merge_buckets(c));
-        if (dbg && dbg->partition)
-            BSPS_CUDA(cudaMemcpyAsync(dbg->partition, c.ly.part, (size_t)(c.pl.p + 1) * c.pl.R * 4,
-                                      cudaMemcpyDeviceToDevice, c.stream));
+        if (c.pl.merge) {
+            BSPS_CUDA(mark(4));
+            BSPS_CUDA(launch_merge_buckets(c));
+        } else {
+            BSPS_CUDA(launch_segment_copy(c));
+            BSPS_CUDA(mark(4));
+            BSPS_CUDA(launch_bucket_sort(c));
+        }
+        if (dbg && dbg->partition)  // the rows of the p - 1 splitters among the sub-bucket splitters' rows
+            BSPS_CUDA(cudaMemcpy2DAsync(dbg->partition, (size_t)c.pl.R * 4, c.ly.part, (size_t)(c.pl.B * c.pl.R * 4),
+                                        (size_t)c.pl.R * 4, (size_t)(c.pl.p + 1), cudaMemcpyDeviceToDevice,
+                                        c.stream));
     } else {
         BSPS_CUDA(launch_route(c));
         BSPS_CUDA(mark(4));

@@ -57,6 +57,8 @@ struct Plan {
     int sampling, dtype, pairs, classify;
     int dup_off;       // keys compared by value alone (no tie-break by position)
     int merge;         // final step: merge of the sorted blocks' segments (Fig. 1 step 12)
+    int seg_route;     // route by the sorted blocks' partition and segment copies (Fig. 1 steps 9-11)
+    int keep_runs;     // the block sorts keep the sorted blocks (merge or seg_route)
     uint64_t seed;
     int64_t B;         // refine: sub-buckets per bucket
     int64_t P;         // vbuckets = p * B
@@ -104,9 +106,11 @@ struct Layout {
     uint32_t *vsize;        // P sub-bucket sizes
     uint64_t *voff;         // P + 1 exclusive offsets
     uint32_t *slow_list;    // sub-buckets too large for the on-chip sort
-    // merge final step (merge == 1); reg_keys / reg_vals then hold the sorted blocks
+    // the sorted blocks and their partition (keep_runs == 1)
+    void *runs;                 // n keys (phi), block k's sorted keys at k*m
+    uint32_t *runs_val;         // n payloads in the same order (pairs)
     uint32_t *rs_phi, *rs_tag;  // R * s: every block's own sample records, before the sample sort
-    uint32_t *part;             // (p + 1) * R: c[k][i] at i * R + k
+    uint32_t *part;             // (P + 1) * R: c[k][v] at v * R + k
 };
 
 struct Ctx {
@@ -144,11 +148,13 @@ bool msd_sample_sort(const Plan &p);                // MSD sample sort is launch
 int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
 // merge final step (Fig. 1 steps 9-12)
-cudaError_t launch_merge_partition(const Ctx &c); // c[k][i] and the bucket sizes (into cursor)
+cudaError_t launch_merge_partition(const Ctx &c); // c[k][v] and the sub-bucket sizes (into cursor)
+cudaError_t launch_segment_copy(const Ctx &c);    // the route as segment copies into the regions
 cudaError_t launch_merge_buckets(const Ctx &c);   // gather + stable merge per bucket
 int merge_cluster(const Plan &pl);                // CTAs per bucket for a bound pl.cap (0: too large)
 int64_t merge_capacity(int cl);                   // keys a cluster of cl CTAs merges
 int64_t merge_runs_max();                         // largest R
+constexpr int64_t kSegRouteRunsMax = 16384;       // largest R of the segment-copy route (shared memory)
 size_t route_keys_smem_bytes(const Plan &pl);
 bool route_keys_splitters_in_smem(const Plan &pl);  // keys-only routing holds the splitters on chip
 

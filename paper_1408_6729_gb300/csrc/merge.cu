@@ -1,12 +1,14 @@
-// merge.cu -- the merge-based final step of Sort_Det_BSP (Fig. 1 steps 9-12).
+// merge.cu -- the end of Sort_Det_BSP on the sorted blocks (Fig. 1 steps 9-12).
 //
 // The blocks sorted for the regular sample (Fig. 1 step 3) are kept in HBM.
 // Step 9: every splitter is located in every sorted block (the partition
 // c[k][i] = number of records of block k preceding S_i), which also gives the
-// bucket sizes.  Steps 10-12: one cluster per bucket gathers the bucket's
-// segments [c[k][i], c[k][i+1]) in block order (the order-preserving route of
-// step 11) and merges them stably, ties going to the earlier block (step 12,
-// Sec. 5.1.1), then writes the bucket to its place in the output.
+// bucket sizes.  Step 11, the route, then moves each bucket's segments
+// [c[k][i], c[k][i+1]) in block order, contiguous runs with no per-key
+// classification, either into the bucket's region for the bucket sort
+// (segment_copy_kernel) or -- the merge final step -- straight into the
+// cluster that merges them stably, ties going to the earlier block (step 12,
+// Sec. 5.1.1), and writes the bucket to its place in the output.
 #include "kernels.cuh"
 #include "segsort_keys.cuh"
 
@@ -41,14 +43,17 @@ __device__ __forceinline__ uint32_t key_of_phi32(int dtype, uint32_t v) {
 // blocks first), and S_i's own block has c = (j+1)*x - 1, the splitter's own
 // sorted position.  A pad splitter follows every key.  Without duplicate
 // handling the comparisons use the key value alone.  Rows 0 and p hold 0 and
-// the block's key count.  The bucket sizes come out as differences of row
-// sums: size_i = sum_k c[k][i+1] - sum_k c[k][i].
+// the block's key count (and the blocks' first and last keys give the
+// smallest and largest key, the outer bounds of the first and last bucket).  The bucket sizes come out as differences of row
+// sums: size_i = sum_k c[k][i+1] - sum_k c[k][i].  The splitters may be the
+// sub-bucket splitters (any sample records): p below is their number plus one.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPartWarps * 32)
 merge_partition_kernel(const uint32_t *__restrict__ runs, const uint32_t *__restrict__ rs_phi,
                        const uint32_t *__restrict__ rs_tag, const uint32_t *__restrict__ vphi,
                        const uint32_t *__restrict__ vtag, int64_t n, int64_t p, int64_t R, int64_t m, int64_t s,
-                       int64_t x, int dup_off, uint32_t *__restrict__ part, uint32_t *__restrict__ cursor) {
+                       int64_t x, int dup_off, uint32_t *__restrict__ part, uint32_t *__restrict__ cursor,
+                       DevStatus *st) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * 32 + lane;
     const bool live = k < R;
@@ -66,6 +71,19 @@ merge_partition_kernel(const uint32_t *__restrict__ runs, const uint32_t *__rest
         }
         const uint32_t tot = warp_sum((uint32_t)len);
         if (lane == 0) atomicAdd(&cursor[p - 1], tot);
+        // the smallest and the largest key (bounds of the first and last
+        // bucket for the bucket sort): the blocks' first and last keys
+        uint32_t mn = 0xffffffffu, mx = 0u;
+        if (len > 0) {
+            mn = runs[lo];
+            mx = runs[lo + len - 1];
+        }
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0 && tot) {
+            atomicMax(&st->ext_min_inv, ~(unsigned long long)mn);
+            atomicMax(&st->ext_max, (unsigned long long)mx);
+        }
     }
     const int64_t rows = p - 1;
     const int64_t nw = (int64_t)gridDim.y * kPartWarps;
@@ -362,6 +380,79 @@ __global__ void __launch_bounds__(kMergeThreads, PAIRS ? 1 : 2) merge_bucket_ker
 }
 
 // ---------------------------------------------------------------------------
+// Step 11 as a copy: sub-bucket v's segments, in block order, into its region
+// (the bucket sort then reads the region as the classification route leaves
+// it: in input order for equal keys).  The segment offsets inside the bucket
+// (a scan over the blocks) and the segments' starts stay in shared memory;
+// each warp copies runs of 32 * kSegItems consecutive positions, every lane
+// finding its positions' segments by walking forward from the run's first.
+// ---------------------------------------------------------------------------
+constexpr int kSegThreads = 512, kSegItems = 8;
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(kSegThreads) segment_copy_kernel(const uint32_t *__restrict__ runs,
+                                                                   const uint32_t *__restrict__ runs_val,
+                                                                   const uint32_t *__restrict__ part,
+                                                                   const uint32_t *__restrict__ vsize, int64_t R,
+                                                                   int64_t m, int64_t cap, uint32_t *reg_keys,
+                                                                   uint32_t *reg_vals, DevStatus *st) {
+    extern __shared__ __align__(16) uint32_t ssm[];
+    uint32_t *soff = ssm, *sst = ssm + R + 1;
+    __shared__ uint32_t tmp[40];
+    const int64_t v = blockIdx.x;
+    const uint32_t N = vsize[v];
+    if (N == 0 || N > cap) return;  // an overflow is already reported
+    const uint32_t *rowa = part + v * R, *rowb = part + (v + 1) * R;
+    for (int64_t k = threadIdx.x; k < R; k += kSegThreads) {
+        const uint32_t x0 = rowa[k], x1 = rowb[k];
+        sst[k] = x0;
+        soff[k] = x1 >= x0 ? x1 - x0 : 0u;
+    }
+    __syncthreads();
+    const uint32_t total = block_excl_scan_smem<kSegThreads>(soff, (int)R, tmp);
+    if (total != N) {  // the segments do not add up to the bucket (never expected): report, touch nothing
+        if (threadIdx.x == 0) {
+            atomicExch(&st->overflow, 1);
+            set_error(st, BSPS_ERR_BUCKET_OVERFLOW);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) soff[R] = N;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *dk = reg_keys + v * cap, *dv = PAIRS ? reg_vals + v * cap : nullptr;
+    constexpr uint32_t RUN = 32 * kSegItems;
+    for (uint32_t base = warp * RUN; base < N; base += (kSegThreads / 32) * RUN) {
+        int64_t l = 0, h = R - 1;  // the last segment starting at or before base
+        while (l < h) {
+            const int64_t mid = (l + h + 1) >> 1;
+            if (soff[mid] <= base) l = mid;
+            else h = mid - 1;
+        }
+        int64_t seg = l;
+        uint32_t kk[kSegItems], vv[kSegItems];
+#pragma unroll
+        for (int u = 0; u < kSegItems; ++u) {
+            const uint32_t q = base + u * 32 + lane;
+            if (q < N) {
+                while (q >= soff[seg + 1]) ++seg;
+                const int64_t src = seg * m + sst[seg] + (q - soff[seg]);
+                kk[u] = runs[src];
+                if constexpr (PAIRS) vv[u] = runs_val[src];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSegItems; ++u) {
+            const uint32_t q = base + u * 32 + lane;
+            if (q < N) {
+                dk[q] = kk[u];
+                if constexpr (PAIRS) dv[q] = vv[u];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int merge_cluster(const Plan &pl) {
@@ -376,21 +467,33 @@ int64_t merge_runs_max() { return kMergeRunsMax; }
 
 cudaError_t launch_merge_partition(const Ctx &c) {
     const Plan &p = c.pl;
-    const int64_t rows = p.p - 1;
+    const int64_t rows = p.P - 1;
     int64_t gy = (rows + kPartWarps * 16 - 1) / (kPartWarps * 16);
     gy = imax64(1, imin64(gy, 65535));
     dim3 grid((unsigned)((p.R + 31) / 32), (unsigned)gy);
     merge_partition_kernel<<<grid, kPartWarps * 32, 0, c.stream>>>(
-        (const uint32_t *)c.ly.reg_keys, c.ly.rs_phi, c.ly.rs_tag, (const uint32_t *)c.ly.vphi, c.ly.vtag, p.n,
-        p.p, p.R, p.m, p.s, p.x, p.dup_off, c.ly.part, c.ly.cursor);
+        (const uint32_t *)c.ly.runs, c.ly.rs_phi, c.ly.rs_tag, (const uint32_t *)c.ly.vphi, c.ly.vtag, p.n,
+        p.P, p.R, p.m, p.s, p.x, p.dup_off, c.ly.part, c.ly.cursor, c.ly.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_copy(const Ctx &c) {
+    const Plan &p = c.pl;
+    const size_t smem = (size_t)(2 * p.R + 1) * 4;
+    auto kern = p.pairs ? segment_copy_kernel<true> : segment_copy_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)p.P, kSegThreads, smem, c.stream>>>((const uint32_t *)c.ly.runs, c.ly.runs_val, c.ly.part,
+                                                         c.ly.vsize, p.R, p.m, p.cap, (uint32_t *)c.ly.reg_keys,
+                                                         c.ly.reg_vals, c.ly.status);
     return cudaGetLastError();
 }
 
 template <bool PAIRS> static cudaError_t launch_merge_buckets_t(const Ctx &c) {
     const Plan &p = c.pl;
     MergeArgs a;
-    a.runs = (const uint32_t *)c.ly.reg_keys;
-    a.runs_val = c.ly.reg_vals;
+    a.runs = (const uint32_t *)c.ly.runs;
+    a.runs_val = c.ly.runs_val;
     a.part = c.ly.part;
     a.vsize = c.ly.vsize;
     a.voff = c.ly.voff;

@@ -172,7 +172,8 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 // key is the start of its value, plus that value's keys in earlier segments,
 // plus its earlier occurrences in this segment (a running count and the lanes
 // of the same value below it).  The records at ranks j*x - 1 are emitted
-// without sorting.  Blocks with more than kLowCardMax values keep their flag
+// without sorting (and, when the sorted block is kept, every key is written at
+// its rank: a stable counting sort).  Blocks with more than kLowCardMax values keep their flag
 // for the stable block sort.
 constexpr int kLowCardThreads = 1024, kLowCardMax = 256, kLowCardSlots = 512;
 constexpr int kLowCardWarps = kLowCardThreads / 32;
@@ -180,7 +181,9 @@ constexpr size_t kLowCardSmem = sizeof(uint32_t) * kLowCardWarps * kLowCardSlots
 template <int DT>
 __global__ void __launch_bounds__(kLowCardThreads, 1)
 run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t s,
-                          int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry) {
+                          int64_t x, typename KeyTraits<DT>::T *sphi, uint32_t *stag, uint32_t *retry,
+                          typename KeyTraits<DT>::T *runs, const uint32_t *__restrict__ vals_in,
+                          uint32_t *runs_val) {
     using K = typename KeyTraits<DT>::T;
     static_assert(sizeof(K) == 4, "32-bit keys");
     constexpr int T = kLowCardThreads, W = kLowCardWarps, NS = kLowCardSlots;
@@ -327,6 +330,10 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
                 const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
                 __syncwarp(act);
                 if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
+                if (runs) {  // the sorted block, kept (a stable counting sort)
+                    runs[lo + g1 - 1] = (K)f;
+                    if (runs_val) runs_val[lo + g1 - 1] = vals_in[lo + e];
+                }
                 if (g1 % xx == 0) {
                     const int64_t j = g1 / xx;
                     sphi[k * s + (j - 1)] = (K)f;
@@ -1001,8 +1008,8 @@ template <int DT, int CL, int ITEMS> static cudaError_t launch_run_sample(const 
     const Plan &p = c.pl;
     kern<<<(unsigned)(p.R * CL), kSortThreads, smem, c.stream>>>(
         (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0],
-        (uint32_t *)&c.ly.status->run_too_big, only, p.merge ? (K *)c.ly.reg_keys : nullptr, c.vals_in,
-        p.merge && p.pairs ? c.ly.reg_vals : nullptr);
+        (uint32_t *)&c.ly.status->run_too_big, only, p.keep_runs ? (K *)c.ly.runs : nullptr, c.vals_in,
+        p.keep_runs && p.pairs ? c.ly.runs_val : nullptr);
     return cudaGetLastError();
 }
 
@@ -1018,7 +1025,7 @@ template <int DT, int CL> static cudaError_t launch_run_sample_keys(const Ctx &c
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)(p.R * CL), 512, smem, c.stream>>>(
         (const K *)c.keys_in, p.n, p.m, p.M, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry,
-        p.merge ? (K *)c.ly.reg_keys : nullptr, c.vals_in, p.merge && p.pairs ? c.ly.reg_vals : nullptr);
+        p.keep_runs ? (K *)c.ly.runs : nullptr, c.vals_in, p.keep_runs && p.pairs ? c.ly.runs_val : nullptr);
     return cudaGetLastError();
 }
 
@@ -1051,12 +1058,13 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
         default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
         }
         if (e != cudaSuccess) return e;
-        if (only && !p.merge) {  // blocks of few distinct keys, before the stable sort (it keeps no sorted block)
+        if (only) {  // blocks of few distinct keys, before the stable sort
             e = cudaFuncSetAttribute(run_sample_lowcard_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kLowCardSmem);
             if (e != cudaSuccess) return e;
             run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, kLowCardSmem, c.stream>>>(
-                (const K *)c.keys_in, p.n, p.m, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
+                (const K *)c.keys_in, p.n, p.m, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry,
+                p.keep_runs ? (K *)c.ly.runs : nullptr, c.vals_in, p.keep_runs && p.pairs ? c.ly.runs_val : nullptr);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

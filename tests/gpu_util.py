@@ -59,8 +59,10 @@ def run_gpu(keys, p, s=0, runs=0, mode=0, seed=0, vals=None, refine=0, capacity_
     pads = torch.full((p,), -1, dtype=torch.int64, device="cuda:0") if debug else None
     mlp_params = torch.zeros(bsps.MLP_PARAMS, dtype=torch.float32, device="cuda:0") if classify else None
     mlp_loss = torch.zeros(2, dtype=torch.float32, device="cuda:0") if classify else None
+    # the partition of the sorted blocks (Fig. 1 step 9), when the call keeps them
+    keeps = final_step or (mode == oracle.REGULAR and keys.dtype.itemsize == 4 and not classify and pl.R <= 16384)
     part = torch.full(((p + 1) * pl.R,), -1, dtype=torch.int32, device="cuda:0") \
-        if (debug and final_step and n > 0) else None
+        if (debug and keeps and n > 0) else None
     rc = bsps.bsps_sort_debug(kin, vin, kout, vout, n, code, prm, sizes, ws, sample=sample,
                               splitters=spl, bucket_of=bo, pad_sizes=pads, mlp_params=mlp_params,
                               mlp_loss=mlp_loss, partition=part)
@@ -98,3 +100,9 @@ def assert_same(gpu, ref, check_sample=True):
         assert np.array_equal(gpu.bucket_of, ref.bucket_of), "per-key buckets differ"
     if gpu.pad_sizes is not None and ref.plan.sampling == oracle.REGULAR:
         assert np.array_equal(gpu.pad_sizes, ref.pad_sizes), "pad counts differ"
+    if getattr(gpu, "partition", None) is not None and getattr(ref, "partition", None) is not None:
+        # the oracle's c[k][i] counts pads too; the GPU's counts the block's keys
+        pl = ref.plan
+        n = gpu.keys.shape[0]
+        real = np.array([max(0, min(int(pl.m), n - k * int(pl.m))) for k in range(int(pl.R))], np.int64)
+        assert np.array_equal(gpu.partition, np.minimum(ref.partition, real[:, None])), "partition differs"

@@ -26,7 +26,8 @@ MODE_IDS = ["regular", "random"]
 
 
 def ref_sort(keys, p, s=0, runs=0, mode=0, seed=0, vals=None):
-    return oracle.sort(keys, p, s, runs, mode, seed, vals=vals, want_bucket_of=keys.shape[0] <= (1 << 22))
+    return oracle.sort(keys, p, s, runs, mode, seed, vals=vals, want_bucket_of=keys.shape[0] <= (1 << 22),
+                       want_partition=mode == oracle.REGULAR)
 
 
 @pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "*.json"))),
