@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t key_of_phi32(int dtype, uint32_t v) {
 // and the warp a contiguous range of splitters.  Block k's own sample records
 // are its sorted positions j*x - 1 (j = 1..s), so the number j of them that
 // precede S_i places c[k][i] in [j*x, (j+1)*x - 1]; j only grows with i, so
-// the lane walks its sample records alongside the splitters.  Inside that
+// the lane gallops forward through its sample records alongside the splitters.  Inside that
 // window of x - 1 keys a binary search decides; a key of block k equal to S_i
 // precedes it exactly when k is below S_i's block (Sec. 5.1.1: tags order
 // blocks first), and S_i's own block has c = (j+1)*x - 1, the splitter's own
@@ -115,7 +115,24 @@ merge_partition_kernel(const uint32_t *__restrict__ runs, const uint32_t *__rest
         const uint32_t ph = vphi[i - 1], tg = vtag[i - 1];
         uint32_t c = 0;
         if (live) {
-            while (j < s && before(j, ph, tg)) ++j;
+            // advance j past this block's records preceding S_i: galloping,
+            // since with many equal keys one splitter can pass hundreds (and
+            // the lanes of a warp pass them at different splitters)
+            if (j < s && before(j, ph, tg)) {
+                int64_t step = 1, hi = j + 1;  // records below hi precede S_i
+                while (hi < s && before(hi, ph, tg)) {
+                    j = hi;
+                    step <<= 1;
+                    hi = imin64(s, j + step);
+                }
+                int64_t lo = j + 1;  // the first record not preceding S_i lies in [lo, hi]
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (before(mid, ph, tg)) lo = mid + 1;
+                    else hi = mid;
+                }
+                j = lo;
+            }
             if (tg >= un) {
                 c = (uint32_t)len;  // a pad splitter follows every key
             } else {

@@ -172,8 +172,9 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 // key is the start of its value, plus that value's keys in earlier segments,
 // plus its earlier occurrences in this segment (a running count and the lanes
 // of the same value below it).  The records at ranks j*x - 1 are emitted
-// without sorting (and, when the sorted block is kept, every key is written at
-// its rank: a stable counting sort).  Blocks with more than kLowCardMax values keep their flag
+// without sorting.  When the sorted block is kept, its keys are written as
+// runs of equal values in position order and every payload at its key's rank
+// (a stable counting sort).  Blocks with more than kLowCardMax values keep their flag
 // for the stable block sort.
 constexpr int kLowCardThreads = 1024, kLowCardMax = 256, kLowCardSlots = 512;
 constexpr int kLowCardWarps = kLowCardThreads / 32;
@@ -191,6 +192,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     __shared__ unsigned long long slot[NS];                 // (1 << 32) | phi, 0 = empty
     __shared__ uint32_t start[NS];                          // sorted start of the slot's value
     __shared__ uint32_t vals[kLowCardMax], sid[kLowCardMax], rank_of[kLowCardMax], tot_sorted[kLowCardMax];
+    __shared__ uint32_t val_of_rank[kLowCardMax];
     __shared__ uint32_t tmp[W + 1];
     __shared__ int ndistinct, overflow;
     const int64_t k = blockIdx.x;
@@ -313,8 +315,24 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
         tot_sorted[tid] = ex;
     }
     __syncthreads();
-    if (tid < nd) start[sid[tid]] = tot_sorted[rank_of[tid]];
+    if (tid < nd) {
+        start[sid[tid]] = tot_sorted[rank_of[tid]];
+        val_of_rank[rank_of[tid]] = vals[tid];
+    }
     __syncthreads();
+    if (runs) {
+        // the sorted block's keys: value of rank r over [start_r, start_r+1),
+        // written in position order
+        for (int64_t t = tid; t < len; t += T) {
+            int l = 0, h = nd - 1;  // the last rank starting at or before t
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (tot_sorted[mid] <= (uint32_t)t) l = mid;
+                else h = mid - 1;
+            }
+            runs[lo + t] = (K)val_of_rank[l];
+        }
+    }
     // pass 2: in position order, sorted rank = start + earlier segments + earlier here
     for (int64_t e0 = seg0; e0 < seg1; e0 += 32 * kAhead) {
         load_ahead(e0);
@@ -330,10 +348,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
                 const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
                 __syncwarp(act);
                 if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
-                if (runs) {  // the sorted block, kept (a stable counting sort)
-                    runs[lo + g1 - 1] = (K)f;
-                    if (runs_val) runs_val[lo + g1 - 1] = vals_in[lo + e];
-                }
+                if (runs_val) runs_val[lo + g1 - 1] = vals_in[lo + e];  // payloads at their ranks
                 if (g1 % xx == 0) {
                     const int64_t j = g1 / xx;
                     sphi[k * s + (j - 1)] = (K)f;
