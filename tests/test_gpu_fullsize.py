@@ -59,7 +59,7 @@ THREADS = max(1, os.cpu_count() or 1)
 
 def _oracle(keys, p, s, runs, mode, seed, vals=None, bucket_of=False):
     return oracle.sort(keys, p, s, runs, mode, seed, vals=vals, want_sample=True,
-                       want_bucket_of=bucket_of, threads=THREADS)
+                       want_bucket_of=bucket_of, threads=THREADS, want_partition=mode == oracle.REGULAR)
 
 
 @pytest.fixture(scope="module")
@@ -77,12 +77,21 @@ def test_headline_uniform_random_2e28(uniform_keys):
     assert ref.bucket_sizes.max() < 1.15 * N / P
 
 
-def test_headline_uniform_regular_2e28(uniform_keys):
+@pytest.fixture(scope="module")
+def regular_ref(uniform_keys):
+    return _oracle(uniform_keys, P, P, P, oracle.REGULAR, 0)
+
+
+@pytest.mark.parametrize("final_step", [0, 1], ids=["bucket_sort", "merge"])
+def test_headline_uniform_regular_2e28(uniform_keys, regular_ref, final_step):
+    """Regular sampling at the stated size, with the partition of every
+    sorted block (Fig. 1 step 9) compared too; ended by the bucket sort or by
+    the paper's merge (Fig. 1 step 12)."""
     keys = uniform_keys
-    ref = _oracle(keys, P, P, P, oracle.REGULAR, 0)
-    gpu = run_gpu(keys, P, P, P, oracle.REGULAR, 0, bucket_of=False)
+    gpu = run_gpu(keys, P, P, P, oracle.REGULAR, 0, bucket_of=False, final_step=final_step)
     assert gpu.plan.sample_size == P * P
-    assert_same(gpu, ref)
+    assert gpu.partition is not None
+    assert_same(gpu, regular_ref)
 
 
 def test_zipf_pairs_regular_2e28():
