@@ -109,7 +109,7 @@ static int make_plan(int64_t n, int dtype, const bsps_params *prm, int pairs, Pl
         pl.B /= 2;
         pl.P = pl.p * pl.B;
     }
-    while (prm->refine == 0 && pl.B > 1 && !pl.pairs && !route_keys_splitters_in_smem(pl)) {
+    while (prm->refine == 0 && pl.B > 1 && !pl.pairs && pl.key_bytes == 4 && !route_keys_splitters_in_smem(pl)) {
         Plan half = pl;
         half.B /= 2;
         half.P = half.p * half.B;

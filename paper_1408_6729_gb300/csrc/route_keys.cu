@@ -18,11 +18,15 @@ namespace bsps {
 constexpr int kRkThreads = 1024;
 constexpr int kEarly = 4;  // buckets per thread reserved before the grouping
 constexpr size_t kRkSmemBudget = 227 * 1024;  // splitters in shared memory up to this size
-// keys per thread (fewer with the network's registers in use; 8-byte keys
-// with the learned classifier: six, so that 8192 sub-buckets' splitters fit
-// shared memory next to the index over the network's output)
+// keys per thread (fewer with the network's registers in use).  8-byte keys
+// with the learned classifier take chunks of 10K with the splitters in global
+// memory (L1-cached): with thousands of sub-buckets the per-chunk work over
+// all of them (scan, reservations) would otherwise weigh as much as the keys,
+// and a key reads one or two splitters.  The splitter tree reads more (skewed
+// keys crowd a few cells of the radix index) and keeps its splitters on chip
+// with chunks of 8K.
 template <typename K, bool LEARNED = false> constexpr int rk_items() {
-    return sizeof(K) == 8 ? (LEARNED ? 6 : 8) : (LEARNED ? 8 : 16);
+    return sizeof(K) == 8 ? (LEARNED ? 10 : 8) : (LEARNED ? 8 : 16);
 }
 template <typename K, bool LEARNED = false> constexpr int rk_chunk() { return kRkThreads * rk_items<K, LEARNED>(); }
 
