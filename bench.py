@@ -40,6 +40,7 @@ WORKLOADS = {
     "uniform_2e28_int32_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=False,
                                             make=lambda n, p, seed: gen.uniform(n, p, seed)),
     "zipf_2e28_int32_pairs_p4096_regular": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096, pairs=True,
+                                               block_sort_kernel="run_sample_lowcard_kernel",
                                                make=lambda n, p, seed: gen.zipf(n, seed=seed)),
     # the regular configurations ended by the paper's merge (Fig. 1 steps 9-12),
     # with the bucket-sort final step timed beside them on the same inputs
@@ -48,6 +49,7 @@ WORKLOADS = {
                                                   make=lambda n, p, seed: gen.uniform(n, p, seed)),
     "zipf_2e28_int32_pairs_p4096_regular_merge": dict(n=1 << 28, p=4096, sampling=0, s=4096, runs=4096,
                                                      pairs=True, final_step=1, compare="sort",
+                                                     block_sort_kernel="run_sample_lowcard_kernel",
                                                      make=lambda n, p, seed: gen.zipf(n, seed=seed)),
     # the merge's kernels on a quarter of the data (16-key segments as at 2^28),
     # for full ncu captures
@@ -115,9 +117,13 @@ COMPARE = {"tree": ("tree", dict(classify=0)), "sort": ("bucket_sort_final_step"
 # from the 2^27-key capture on [0, 2^30) (65,536-key buckets spanning 2^19
 # values on clusters of 8, as at 2^28);
 # both kernels stream every key once, so bytes per key carry over to 2^28
-NCU_TRAFFIC = {"route_keys_kernel": ((271.315968e6 + 223.367168e6) / (1 << 26), "ac9e5a62a1b9d446"),
-               "bucket_keys32_kernel": ((537.311488e6 + 487.655424e6) / (1 << 27), "ceb023d4ec9e106a")}
+# (bytes per key, source hash, payloads) of each capture; the segment copy's
+# from the 2^26-pair Zipf capture (4096 buckets of 16-key segments, as at 2^28)
+NCU_TRAFFIC = {"route_keys_kernel": ((271.608576e6 + 223.674880e6) / (1 << 26), "8baca4c618da453f", False),
+               "bucket_keys32_kernel": ((537.311488e6 + 487.655424e6) / (1 << 27), "ceb023d4ec9e106a", False),
+               "segment_copy_kernel": ((613.273600e6 + 498.500864e6) / (1 << 26), "cefd083be8a0bc0e", True)}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
+                 "segment_copy_kernel": ["paper_1408_6729_gb300/csrc/merge.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",
                                        "paper_1408_6729_gb300/csrc/classify.cuh",
                                        "paper_1408_6729_gb300/csrc/kernels.cuh"],
@@ -547,10 +553,13 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     key_bytes = 8 if wl.get("dtype") == "f64" else 4
     kb = key_bytes + (4 if wl["pairs"] else 0)
     merge = wl.get("final_step", 0) == 1
+    # regular sampling of 4-byte keys keeps the sorted blocks and routes by
+    # their partition and segment copies (Fig. 1 steps 9-11)
+    keep = wl["sampling"] == 0 and key_bytes == 4 and not wl.get("classify")
     # (kernel, algorithmic bytes) of every phase that moves all the keys
     model = {}
-    if wl["sampling"] == 0:  # the block sort reads every key (and keeps the sorted blocks for the merge)
-        model["sample"] = ("run_sample_keys_kernel", n * (2 * kb if merge else key_bytes))
+    if wl["sampling"] == 0:  # the block sort reads every key (and writes the sorted blocks when it keeps them)
+        model["sample"] = (wl.get("block_sort_kernel", "run_sample_keys_kernel"), n * (2 * kb if keep else key_bytes))
     if merge:
         model["bucket_sort"] = ("merge_bucket_kernel", n * 2 * kb)
     else:
@@ -558,13 +567,15 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
             kern = PHASE_KERNEL[(ph, bool(wl["pairs"]))]
             if key_bytes == 8 and not wl["pairs"]:
                 kern = PHASE_KERNEL_F64.get(ph, kern)
+            if ph == "route" and keep:
+                kern = "segment_copy_kernel"
             model[ph] = (kern, n * 2 * kb)
     dom = max(model, key=lambda k: per_step[k])
     kern, alg_bytes = model[dom]
     achieved = alg_bytes / (per_step[dom] * 1e-3) / 1e9
     traffic = None
     if kern in NCU_TRAFFIC and NCU_TRAFFIC[kern][1] == source_hash(KERNEL_SOURCE[kern]) and \
-            wl.get("dtype") != "f64" and not wl["pairs"]:
+            wl.get("dtype") != "f64" and bool(wl["pairs"]) == NCU_TRAFFIC[kern][2]:
         traffic = NCU_TRAFFIC[kern][0] * n
     ms_step = elapsed_ms / args.steps
     value = world * n / (ms_step * 1e-3)
