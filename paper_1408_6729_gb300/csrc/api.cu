@@ -272,9 +272,11 @@ static void to_public(const Plan &p, bsps_plan *out) {
 
 // Kernels one call launches (the sample sort launches all its pass slots;
 // slots whose byte position is constant return at once).
-static int kernels_per_call(const Plan &pl) {
+static int kernels_per_call(const Ctx &c) {
+    const Plan &pl = c.pl;
     int k = 1;                                   // sample (random draw or block sort)
     if (run_keys_cluster(pl)) k += 2;            // keys-only and few-values block samplers before the stable one
+    if (counting_block_sort(c)) k += 1;          // the counting sort's tags
     if (pl.sampling == BSPS_RANDOM && pl.sample_size == 0) k = 0;
     k += 2 + (pl.lsd_tiles > 0 ? 3 * pl.lsd_npos : 0);  // histogram, pass table, passes
     if (msd_sample_sort(pl)) k += 4;                 // MSD histogram, plan, scatter, bin sorts
@@ -375,7 +377,7 @@ static int run(const void *keys_in, const uint32_t *vals_in, void *keys_out, uin
     }
     BSPS_CUDA(mark(5));
     if (dbg) BSPS_CUDA(launch_debug(c));
-    if (dbg && dbg->launches) *dbg->launches = kernels_per_call(c.pl) + debug_kernels(c);
+    if (dbg && dbg->launches) *dbg->launches = kernels_per_call(c) + debug_kernels(c);
     return BSPS_OK;
 }
 

@@ -134,8 +134,9 @@ struct BucketKeys32 {
                 : "memory");
         return done != 0;
     }
+    template <typename Xf>
     __device__ static void load_staged(Smem &sm, K (&k)[ITEMS], const K *__restrict__ src, int n, K *buf,
-                                       DevStatus *st) {
+                                       DevStatus *st, Xf xf) {
         const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
         const uint32_t bytes = (uint32_t)((n * (int)sizeof(K) + 15) & ~15);
         if (threadIdx.x == 0) {
@@ -162,7 +163,7 @@ struct BucketKeys32 {
             const int q = j * T + (int)threadIdx.x;
             if (q * 4 < n) {
                 const uint4 w = *reinterpret_cast<const uint4 *>(buf + q * 4);
-                k[j * 4 + 0] = w.x; k[j * 4 + 1] = w.y; k[j * 4 + 2] = w.z; k[j * 4 + 3] = w.w;
+                k[j * 4 + 0] = xf(w.x); k[j * 4 + 1] = xf(w.y); k[j * 4 + 2] = xf(w.z); k[j * 4 + 3] = xf(w.w);
             }
         }
     }
@@ -385,9 +386,14 @@ struct BucketKeys32 {
     // multiple of 4 keys stays inside the caller's region; lo <= key <= hi,
     // lo < hi) and calls emit(position, key) for each.  Returns false when
     // the sub-bucket goes to the stable sort, which rewrites every position.
-    template <typename Emit>
+    // xf maps each loaded word to the key sorted (the order-preserving phi of
+    // the caller's key type; by default the words are already keys).
+    struct Same {
+        __device__ K operator()(K v) const { return v; }
+    };
+    template <typename Emit, typename Xf = Same>
     __device__ static bool run(unsigned char *smem, const K *__restrict__ src, int64_t cnt, K lo, K hi, Emit emit,
-                               DevStatus *st) {
+                               DevStatus *st, Xf xf = Xf()) {
         Smem &sm = *reinterpret_cast<Smem *>(smem);
         K *regA = reinterpret_cast<K *>(smem + kSmemHead);
         K *regB = reinterpret_cast<K *>(smem + kSmemHead + kBytesA);
@@ -397,7 +403,7 @@ struct BucketKeys32 {
         K k[ITEMS];
         if constexpr (CL == 1) {
             const int n = (int)cnt;
-            load_staged(sm, k, src, n, regB, st);
+            load_staged(sm, k, src, n, regB, st, xf);
             auto mine = [&](int i) { return lidx(i) < n; };
             if (!count_sort(k, mine, lo, hi - lo, regB, reinterpret_cast<uint32_t *>(regA), sm.tmp, sm.list))
                 return false;
@@ -408,7 +414,7 @@ struct BucketKeys32 {
             const int c = (int)cluster.block_rank();
             const int e0 = c * (int)share;
             const int mycnt = (int)imax64(0, imin64(share, cnt - e0));
-            load_staged(sm, k, src + e0, mycnt, regB, st);  // (the receive buffer is free until the barrier below)
+            load_staged(sm, k, src + e0, mycnt, regB, st, xf);  // (the receive buffer is free until the barrier below)
             auto mine = [&](int i) { return lidx(i) < mycnt; };
             const int bits = bit_length<K>(hi - lo);
             const int shift = bits > 8 ? bits - 8 : 0;

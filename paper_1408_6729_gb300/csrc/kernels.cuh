@@ -146,6 +146,7 @@ size_t mlp_opt_bytes();
 size_t route_smem_bytes(const Plan &pl);
 bool msd_sample_sort(const Plan &p);                // MSD sample sort is launched (32-bit keys, large samples)
 int run_keys_cluster(const Plan &p);               // keys-only block sort for regular sampling (0: not used)
+bool counting_block_sort(const Ctx &c);            // kept blocks sorted by the counting sort (and tags recovered)
 cudaError_t launch_route_keys(const Ctx &c);      // keys without payloads, one pass
 // merge final step (Fig. 1 steps 9-12)
 cudaError_t launch_merge_partition(const Ctx &c); // c[k][v] and the sub-bucket sizes (into cursor)

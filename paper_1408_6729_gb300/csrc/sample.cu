@@ -4,6 +4,7 @@
 #include "mlp.cuh"
 #include "segsort.cuh"
 #include "segsort_keys.cuh"
+#include "bucket_keys32.cuh"
 
 namespace bsps {
 
@@ -155,6 +156,176 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
     auto one_value = [](uint64_t mn, uint64_t mx) { return (mn >> 32) == (mx >> 32); };
     if (!SS::run_load(smem_raw, len, 0ull, ~0ull, loadf, emit, one_value) && threadIdx.x == 0)
         atomicExch(&retry[k], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// The same sample from the counting sort, when the sorted blocks are kept: a
+// block's 32-bit keys (their phi, as they load) are sorted by the keys-only
+// counting sort of bucket_keys32.cuh -- the bucket sort's own kernel -- into
+// the sorted block, and the keys at the sampled ranks are recorded.  Their
+// tags (input positions) come from run_sample_tags_kernel.  Equal keys leave
+// the counting sort in no particular order, which neither the sorted block
+// (keys only) nor the tags (recovered in input order) can reveal.  A block
+// the counting sort gives back, or with many repeated keys, is flagged for the
+// few-values sampler and the stable block sort.
+// ---------------------------------------------------------------------------
+template <int DT> struct PhiOf {
+    __device__ uint32_t operator()(uint32_t u) const { return (uint32_t)KeyTraits<DT>::phi(u); }
+};
+
+template <int DT, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
+run_sample_count_kernel(const uint32_t *__restrict__ keys, int64_t n, int64_t m, int64_t M, int64_t s, int64_t x,
+                        uint32_t *sphi, uint32_t *stag, uint32_t *retry, uint32_t *runs, DevStatus *st) {
+    using SS = BucketKeys32<CL>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t k = blockIdx.x / CL;
+    const int64_t lo = k * m;
+    const int64_t len = lo < n ? imin64(m, n - lo) : 0;
+    if (blockIdx.x % CL == 0) {  // pads: sorted positions len..M-1, in tag order
+        for (int64_t j = 1 + threadIdx.x; j <= s; j += blockDim.x) {
+            const int64_t pos = j * x - 1;
+            if (pos >= len) {
+                sphi[k * s + (j - 1)] = 0xffffffffu;
+                stag[k * s + (j - 1)] = (uint32_t)(n + k * M + pos);
+            }
+        }
+    }
+    if (len == 0) return;
+    {
+        // many repeats among 64 evenly spaced keys: the few-values sampler
+        // (every CTA of the cluster reads the same keys and decides alike)
+        __shared__ uint32_t probe[64];
+        __shared__ int repeats;
+        if (threadIdx.x < 64) probe[threadIdx.x] = keys[lo + threadIdx.x * len / 64];
+        if (threadIdx.x == 0) repeats = 0;
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            bool seen = false;
+            for (int j = 0; j < (int)threadIdx.x; ++j) seen |= probe[j] == probe[threadIdx.x];
+            if (seen) atomicAdd(&repeats, 1);
+        }
+        __syncthreads();
+        if (len >= 64 && repeats > 8) {
+            if (threadIdx.x == 0) retry[k] = 1u;
+            return;
+        }
+    }
+    const uint32_t xx = (uint32_t)x;
+    auto emit = [&](uint32_t pos, uint32_t key) {
+        runs[lo + pos] = key;
+        if ((pos + 1) % xx == 0) sphi[k * s + (pos + 1) / xx - 1] = key;
+    };
+    typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
+    if (threadIdx.x == 0) sm.stalled = 0;
+    __syncthreads();
+    bool done = SS::run(smem_raw, keys + lo, len, 0u, 0xffffffffu, emit, st, PhiOf<DT>());
+    __syncthreads();
+    if (sm.stalled) {  // the staged load's wait ran out: wait for the copy once more, give the block back
+        SS::wait_staged(sm, kSpinLimit);
+        done = false;
+    }
+    if (!done && threadIdx.x == 0) retry[k] = 1u;
+}
+
+// Tags of the sampled keys of a block sorted by run_sample_count_kernel: the
+// sampled rank r = j*x - 1 holds key v, the o-th (o = r - first rank of v) of
+// the block's keys equal to v, in input order (Sec. 5.1.1).  A key that occurs
+// once in the block is found by one pass over the block's input through a
+// shared-memory hash of the sampled keys; a repeated one by a warp counting
+// its occurrences in input order.  A block with more sampled keys than the
+// hash holds, or more repeated ones than the list holds, goes to the stable
+// block sort.
+constexpr int kTagThreads = 1024, kTagSlotBits = 14, kTagSlots = 1 << kTagSlotBits, kTagDupMax = 2048;
+constexpr size_t kTagSmem = sizeof(unsigned long long) * kTagSlots + sizeof(uint32_t) * kTagDupMax;
+
+template <int DT>
+__global__ void __launch_bounds__(kTagThreads, 1)
+run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ runs, int64_t n, int64_t m,
+                       int64_t s, int64_t x, uint32_t *stag, uint32_t *retry) {
+    extern __shared__ __align__(16) unsigned char tag_smem[];
+    unsigned long long *H = reinterpret_cast<unsigned long long *>(tag_smem);  // key << 32 | j, 0 = empty
+    uint32_t *dup = reinterpret_cast<uint32_t *>(H + kTagSlots);
+    __shared__ uint32_t ndup;
+    const int64_t k = blockIdx.x;
+    if (retry[k]) return;  // the few-values sampler or the stable sort takes it
+    const int64_t lo = k * m;
+    const int64_t len = lo < n ? imin64(m, n - lo) : 0;
+    if (len == 0) return;
+    const int64_t js = len / x;  // sampled ranks j*x - 1 inside the block's keys
+    if (js > kTagSlots / 2) {
+        if (threadIdx.x == 0) retry[k] = 1u;
+        return;
+    }
+    const uint32_t *blk = runs + lo;
+    auto slot_of = [](uint32_t v) { return (v * 0x9e3779b1u) >> (32 - kTagSlotBits); };
+    for (int i = threadIdx.x; i < kTagSlots; i += kTagThreads) H[i] = 0ull;
+    if (threadIdx.x == 0) ndup = 0;
+    __syncthreads();
+    for (int64_t j = 1 + threadIdx.x; j <= js; j += kTagThreads) {
+        const int64_t r = j * x - 1;
+        const uint32_t v = blk[r];
+        int64_t a = 0, b = r;  // first rank holding v
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if (blk[mid] < v) a = mid + 1;
+            else b = mid;
+        }
+        const bool single = a == r && (r + 1 == len || blk[r + 1] != v);
+        if (single) {
+            const unsigned long long e = (unsigned long long)v << 32 | (uint32_t)j;
+            uint32_t h = slot_of(v);
+            for (int probe = 0; probe < kTagSlots; ++probe, h = (h + 1) & (kTagSlots - 1))
+                if (atomicCAS(&H[h], 0ull, e) == 0ull) break;
+        } else {
+            const uint32_t at = atomicAdd(&ndup, 1u);
+            if (at < kTagDupMax) dup[at] = (uint32_t)j;
+        }
+    }
+    __syncthreads();
+    if (ndup > kTagDupMax) {  // uniform
+        if (threadIdx.x == 0) retry[k] = 1u;
+        return;
+    }
+    // keys that occur once: one pass over the block's input
+    for (int64_t t = threadIdx.x; t < len; t += kTagThreads) {
+        const uint32_t u = (uint32_t)KeyTraits<DT>::phi(keys[lo + t]);
+        uint32_t h = slot_of(u);
+        for (int probe = 0; probe < kTagSlots; ++probe, h = (h + 1) & (kTagSlots - 1)) {
+            const unsigned long long e = H[h];
+            if (e == 0ull) break;
+            if ((uint32_t)(e >> 32) == u) {
+                stag[k * s + ((uint32_t)e - 1)] = (uint32_t)(lo + t);
+                break;
+            }
+        }
+    }
+    // repeated keys: the o-th occurrence in input order, one warp each
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t d = warp; d < ndup; d += kTagThreads / 32) {
+        const int64_t j = dup[d], r = j * x - 1;
+        const uint32_t v = blk[r];
+        int64_t a = 0, b = r;
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if (blk[mid] < v) a = mid + 1;
+            else b = mid;
+        }
+        uint32_t o = (uint32_t)(r - a);
+        for (int64_t base = 0; base < len; base += 32) {
+            const int64_t t = base + lane;
+            const bool eq = t < len && (uint32_t)KeyTraits<DT>::phi(keys[lo + t]) == v;
+            const uint32_t bal = __ballot_sync(0xffffffffu, eq);
+            const uint32_t c = (uint32_t)__popc(bal);
+            if (o < c) {
+                uint32_t bits = bal;
+                for (uint32_t q = 0; q < o; ++q) bits &= bits - 1;  // drop the o lowest
+                if (lane == 0) stag[k * s + (j - 1)] = (uint32_t)(lo + base + __ffs(bits) - 1);
+                break;
+            }
+            o -= c;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1044,6 +1215,35 @@ template <int DT, int CL> static cudaError_t launch_run_sample_keys(const Ctx &c
     return cudaGetLastError();
 }
 
+// the kept blocks are sorted by the counting sort: whole 16-byte groups of
+// keys in every block and in the input (its bulk copies read nothing past n)
+bool counting_block_sort(const Ctx &c) {
+    const Plan &p = c.pl;
+    return p.keep_runs && p.key_bytes == 4 && run_keys_cluster(p) != 0 && p.m % 4 == 0 && p.n % 4 == 0 &&
+           ((uintptr_t)c.keys_in & 15) == 0;
+}
+
+template <int DT, int CL> static cudaError_t launch_run_sample_count(const Ctx &c) {
+    using SS = BucketKeys32<CL>;
+    const size_t smem = SS::smem_bytes();
+    auto kern = run_sample_count_kernel<DT, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const Plan &p = c.pl;
+    e = cudaMemsetAsync(c.ly.run_retry, 0, (size_t)p.R * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(p.R * CL), 512, smem, c.stream>>>((const uint32_t *)c.keys_in, p.n, p.m, p.M, p.s, p.x,
+                                                        (uint32_t *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry,
+                                                        (uint32_t *)c.ly.runs, c.ly.status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(run_sample_tags_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTagSmem);
+    if (e != cudaSuccess) return e;
+    run_sample_tags_kernel<DT><<<(unsigned)p.R, kTagThreads, kTagSmem, c.stream>>>(
+        (const uint32_t *)c.keys_in, (const uint32_t *)c.ly.runs, p.n, p.m, p.s, p.x, c.ly.stag[0], c.ly.run_retry);
+    return cudaGetLastError();
+}
+
 // cluster size of the keys-only block sort (0: not used)
 int run_keys_cluster(const Plan &p) {
     if (p.sampling != BSPS_REGULAR || p.key_bytes != 4 || p.m >= ((int64_t)1 << 32)) return 0;
@@ -1065,12 +1265,22 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
     const uint32_t *only = nullptr;
     if constexpr (sizeof(K) == 4) {
         cudaError_t e = cudaSuccess;
-        switch (run_keys_cluster(p)) {
-        case 0: break;
-        case 1: e = launch_run_sample_keys<DT, 1>(c); only = c.ly.run_retry; break;
-        case 2: e = launch_run_sample_keys<DT, 2>(c); only = c.ly.run_retry; break;
-        case 4: e = launch_run_sample_keys<DT, 4>(c); only = c.ly.run_retry; break;
-        default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
+        if (counting_block_sort(c)) {
+            switch (run_keys_cluster(p)) {
+            case 1: e = launch_run_sample_count<DT, 1>(c); break;
+            case 2: e = launch_run_sample_count<DT, 2>(c); break;
+            case 4: e = launch_run_sample_count<DT, 4>(c); break;
+            default: e = launch_run_sample_count<DT, 8>(c); break;
+            }
+            only = c.ly.run_retry;
+        } else {
+            switch (run_keys_cluster(p)) {
+            case 0: break;
+            case 1: e = launch_run_sample_keys<DT, 1>(c); only = c.ly.run_retry; break;
+            case 2: e = launch_run_sample_keys<DT, 2>(c); only = c.ly.run_retry; break;
+            case 4: e = launch_run_sample_keys<DT, 4>(c); only = c.ly.run_retry; break;
+            default: e = launch_run_sample_keys<DT, 8>(c); only = c.ly.run_retry; break;
+            }
         }
         if (e != cudaSuccess) return e;
         if (only) {  // blocks of few distinct keys, before the stable sort
