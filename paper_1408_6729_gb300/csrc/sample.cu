@@ -159,7 +159,8 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 }
 
 // ---------------------------------------------------------------------------
-// The same sample from the counting sort, when the sorted blocks are kept: a
+// The same sample from the counting sort, when the sorted blocks of keys
+// without payloads are kept: a
 // block's 32-bit keys (their phi, as they load) are sorted by the keys-only
 // counting sort of bucket_keys32.cuh -- the bucket sort's own kernel -- into
 // the sorted block, and the keys at the sampled ranks are recorded.  Their
@@ -1215,12 +1216,13 @@ template <int DT, int CL> static cudaError_t launch_run_sample_keys(const Ctx &c
     return cudaGetLastError();
 }
 
-// the kept blocks are sorted by the counting sort: whole 16-byte groups of
-// keys in every block and in the input (its bulk copies read nothing past n)
+// the kept blocks are sorted by the counting sort: keys without payloads
+// (it moves keys only), whole 16-byte groups of keys in every block and in
+// the input (its bulk copies read nothing past n)
 bool counting_block_sort(const Ctx &c) {
     const Plan &p = c.pl;
-    return p.keep_runs && p.key_bytes == 4 && run_keys_cluster(p) != 0 && p.m % 4 == 0 && p.n % 4 == 0 &&
-           ((uintptr_t)c.keys_in & 15) == 0;
+    return p.keep_runs && !p.pairs && p.key_bytes == 4 && run_keys_cluster(p) != 0 && p.m % 4 == 0 &&
+           p.n % 4 == 0 && ((uintptr_t)c.keys_in & 15) == 0;
 }
 
 template <int DT, int CL> static cudaError_t launch_run_sample_count(const Ctx &c) {
