@@ -163,8 +163,8 @@ run_sample_keys_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64
 // without payloads are kept: a
 // block's 32-bit keys (their phi, as they load) are sorted by the keys-only
 // counting sort of bucket_keys32.cuh -- the bucket sort's own kernel -- into
-// the sorted block, and the keys at the sampled ranks are recorded.  Their
-// tags (input positions) come from run_sample_tags_kernel.  Equal keys leave
+// the sorted block; run_sample_tags_kernel then reads the keys at the sampled
+// ranks and finds their tags (input positions).  Equal keys leave
 // the counting sort in no particular order, which neither the sorted block
 // (keys only) nor the tags (recovered in input order) can reveal.  A block
 // the counting sort gives back, or with many repeated keys, is flagged for the
@@ -178,6 +178,7 @@ template <int DT, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(512, 2)
 run_sample_count_kernel(const uint32_t *__restrict__ keys, int64_t n, int64_t m, int64_t M, int64_t s, int64_t x,
                         uint32_t *sphi, uint32_t *stag, uint32_t *retry, uint32_t *runs, DevStatus *st) {
+    // (sphi, stag: the pads' records only; the keys' records come from run_sample_tags_kernel)
     using SS = BucketKeys32<CL>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t k = blockIdx.x / CL;
@@ -212,11 +213,7 @@ run_sample_count_kernel(const uint32_t *__restrict__ keys, int64_t n, int64_t m,
             return;
         }
     }
-    const uint32_t xx = (uint32_t)x;
-    auto emit = [&](uint32_t pos, uint32_t key) {
-        runs[lo + pos] = key;
-        if ((pos + 1) % xx == 0) sphi[k * s + (pos + 1) / xx - 1] = key;
-    };
+    auto emit = [&](uint32_t pos, uint32_t key) { runs[lo + pos] = key; };
     typename SS::Smem &sm = *reinterpret_cast<typename SS::Smem *>(smem_raw);
     if (threadIdx.x == 0) sm.stalled = 0;
     __syncthreads();
@@ -237,16 +234,24 @@ run_sample_count_kernel(const uint32_t *__restrict__ keys, int64_t n, int64_t m,
 // its occurrences in input order.  A block with more sampled keys than the
 // hash holds, or more repeated ones than the list holds, goes to the stable
 // block sort.
-constexpr int kTagThreads = 1024, kTagSlotBits = 14, kTagSlots = 1 << kTagSlotBits, kTagDupMax = 2048;
-constexpr size_t kTagSmem = sizeof(unsigned long long) * kTagSlots + sizeof(uint32_t) * kTagDupMax;
+constexpr int kTagThreads = 1024, kTagSlotBitsMax = 14, kTagDupMax = 2048;
+// hash slots: a power of two at least twice the sampled keys of a block
+static int tag_slot_bits(const Plan &p) {
+    const int64_t js = p.m / p.x;
+    int b = 10;
+    while (b < kTagSlotBitsMax && ((int64_t)1 << b) < 2 * js) ++b;
+    return b;
+}
+static size_t tag_smem(int bits) { return sizeof(unsigned long long) * ((size_t)1 << bits) + sizeof(uint32_t) * kTagDupMax; }
 
 template <int DT>
 __global__ void __launch_bounds__(kTagThreads, 1)
 run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ runs, int64_t n, int64_t m,
-                       int64_t s, int64_t x, uint32_t *stag, uint32_t *retry) {
-    extern __shared__ __align__(16) unsigned char tag_smem[];
-    unsigned long long *H = reinterpret_cast<unsigned long long *>(tag_smem);  // key << 32 | j, 0 = empty
-    uint32_t *dup = reinterpret_cast<uint32_t *>(H + kTagSlots);
+                       int64_t s, int64_t x, int slot_bits, uint32_t *sphi, uint32_t *stag, uint32_t *retry) {
+    extern __shared__ __align__(16) unsigned char tag_raw[];
+    const int slots = 1 << slot_bits;
+    unsigned long long *H = reinterpret_cast<unsigned long long *>(tag_raw);  // key << 32 | j, 0 = empty
+    uint32_t *dup = reinterpret_cast<uint32_t *>(H + slots);
     __shared__ uint32_t ndup;
     const int64_t k = blockIdx.x;
     if (retry[k]) return;  // the few-values sampler or the stable sort takes it
@@ -254,29 +259,25 @@ run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__rest
     const int64_t len = lo < n ? imin64(m, n - lo) : 0;
     if (len == 0) return;
     const int64_t js = len / x;  // sampled ranks j*x - 1 inside the block's keys
-    if (js > kTagSlots / 2) {
+    if (js > slots / 2) {
         if (threadIdx.x == 0) retry[k] = 1u;
         return;
     }
     const uint32_t *blk = runs + lo;
-    auto slot_of = [](uint32_t v) { return (v * 0x9e3779b1u) >> (32 - kTagSlotBits); };
-    for (int i = threadIdx.x; i < kTagSlots; i += kTagThreads) H[i] = 0ull;
+    auto slot_of = [&](uint32_t v) { return (v * 0x9e3779b1u) >> (32 - slot_bits); };
+    for (int i = threadIdx.x; i < slots; i += kTagThreads) H[i] = 0ull;
     if (threadIdx.x == 0) ndup = 0;
     __syncthreads();
     for (int64_t j = 1 + threadIdx.x; j <= js; j += kTagThreads) {
         const int64_t r = j * x - 1;
         const uint32_t v = blk[r];
-        int64_t a = 0, b = r;  // first rank holding v
-        while (a < b) {
-            const int64_t mid = (a + b) >> 1;
-            if (blk[mid] < v) a = mid + 1;
-            else b = mid;
-        }
-        const bool single = a == r && (r + 1 == len || blk[r + 1] != v);
+        sphi[k * s + (j - 1)] = v;
+        // the key occurs once unless a neighbour holds it too
+        const bool single = (r == 0 || blk[r - 1] != v) && (r + 1 == len || blk[r + 1] != v);
         if (single) {
             const unsigned long long e = (unsigned long long)v << 32 | (uint32_t)j;
             uint32_t h = slot_of(v);
-            for (int probe = 0; probe < kTagSlots; ++probe, h = (h + 1) & (kTagSlots - 1))
+            for (int probe = 0; probe < slots; ++probe, h = (h + 1) & (slots - 1))
                 if (atomicCAS(&H[h], 0ull, e) == 0ull) break;
         } else {
             const uint32_t at = atomicAdd(&ndup, 1u);
@@ -292,7 +293,7 @@ run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__rest
     for (int64_t t = threadIdx.x; t < len; t += kTagThreads) {
         const uint32_t u = (uint32_t)KeyTraits<DT>::phi(keys[lo + t]);
         uint32_t h = slot_of(u);
-        for (int probe = 0; probe < kTagSlots; ++probe, h = (h + 1) & (kTagSlots - 1)) {
+        for (int probe = 0; probe < slots; ++probe, h = (h + 1) & (slots - 1)) {
             const unsigned long long e = H[h];
             if (e == 0ull) break;
             if ((uint32_t)(e >> 32) == u) {
@@ -1239,10 +1240,13 @@ template <int DT, int CL> static cudaError_t launch_run_sample_count(const Ctx &
                                                         (uint32_t *)c.ly.runs, c.ly.status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(run_sample_tags_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTagSmem);
+    const int bits = tag_slot_bits(p);
+    e = cudaFuncSetAttribute(run_sample_tags_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tag_smem(kTagSlotBitsMax));
     if (e != cudaSuccess) return e;
-    run_sample_tags_kernel<DT><<<(unsigned)p.R, kTagThreads, kTagSmem, c.stream>>>(
-        (const uint32_t *)c.keys_in, (const uint32_t *)c.ly.runs, p.n, p.m, p.s, p.x, c.ly.stag[0], c.ly.run_retry);
+    run_sample_tags_kernel<DT><<<(unsigned)p.R, kTagThreads, tag_smem(bits), c.stream>>>(
+        (const uint32_t *)c.keys_in, (const uint32_t *)c.ly.runs, p.n, p.m, p.s, p.x, bits,
+        (uint32_t *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry);
     return cudaGetLastError();
 }
 
