@@ -228,21 +228,26 @@ run_sample_count_kernel(const uint32_t *__restrict__ keys, int64_t n, int64_t m,
 
 // Tags of the sampled keys of a block sorted by run_sample_count_kernel: the
 // sampled rank r = j*x - 1 holds key v, the o-th (o = r - first rank of v) of
-// the block's keys equal to v, in input order (Sec. 5.1.1).  A key that occurs
-// once in the block is found by one pass over the block's input through a
-// shared-memory hash of the sampled keys; a repeated one by a warp counting
-// its occurrences in input order.  A block with more sampled keys than the
-// hash holds, or more repeated ones than the list holds, goes to the stable
-// block sort.
-constexpr int kTagThreads = 1024, kTagSlotBitsMax = 14, kTagDupMax = 2048;
-// hash slots: a power of two at least twice the sampled keys of a block
+// the block's keys equal to v in input order (Sec. 5.1.1), so its tag is the
+// o-th smallest input position holding v.  One pass over the block's input
+// serves every sampled key: a key that occurs once in the block is found
+// through a shared-memory hash of those keys; the positions of a repeated one
+// are gathered into a list (a second hash gives each such key its list) and
+// the o-th smallest is picked.  A block whose sampled keys overflow the
+// hash, or whose repeated keys occur too often (more than kTagRunMax times
+// each, or too many positions in all), goes to the stable block sort.
+constexpr int kTagThreads = 1024, kTagSlotBitsMax = 14, kTagDupBits = 9, kTagDupSlots = 1 << kTagDupBits,
+              kTagListMax = 4096, kTagAhead = 8, kTagRunMax = 32;
+// hash slots: a power of two at least four times the sampled keys of a block
 static int tag_slot_bits(const Plan &p) {
     const int64_t js = p.m / p.x;
     int b = 10;
-    while (b < kTagSlotBitsMax && ((int64_t)1 << b) < 2 * js) ++b;
+    while (b < kTagSlotBitsMax && ((int64_t)1 << b) < 4 * js) ++b;
     return b;
 }
-static size_t tag_smem(int bits) { return sizeof(unsigned long long) * ((size_t)1 << bits) + sizeof(uint32_t) * kTagDupMax; }
+static size_t tag_smem(int bits) {
+    return sizeof(unsigned long long) * (((size_t)1 << bits) + kTagDupSlots) + sizeof(uint32_t) * (kTagDupSlots * 3 + kTagListMax);
+}
 
 template <int DT>
 __global__ void __launch_bounds__(kTagThreads, 1)
@@ -251,82 +256,158 @@ run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__rest
     extern __shared__ __align__(16) unsigned char tag_raw[];
     const int slots = 1 << slot_bits;
     unsigned long long *H = reinterpret_cast<unsigned long long *>(tag_raw);  // key << 32 | j, 0 = empty
-    uint32_t *dup = reinterpret_cast<uint32_t *>(H + slots);
-    __shared__ uint32_t ndup;
+    unsigned long long *D = H + slots;                                       // key << 32 | (d + 1): repeated keys
+    uint32_t *dcount = reinterpret_cast<uint32_t *>(D + kTagDupSlots);       // occurrences of repeated key d
+    uint32_t *dstart = dcount + kTagDupSlots;                                // its list's start
+    uint32_t *dfill = dstart + kTagDupSlots;                                 // positions gathered so far
+    uint32_t *list = dfill + kTagDupSlots;                                   // the positions
+    __shared__ uint32_t ndist, nlist, bad;
     const int64_t k = blockIdx.x;
     if (retry[k]) return;  // the few-values sampler or the stable sort takes it
     const int64_t lo = k * m;
     const int64_t len = lo < n ? imin64(m, n - lo) : 0;
     if (len == 0) return;
     const int64_t js = len / x;  // sampled ranks j*x - 1 inside the block's keys
-    if (js > slots / 2) {
+    if (js == 0) return;
+    if (4 * js > slots) {
         if (threadIdx.x == 0) retry[k] = 1u;
         return;
     }
     const uint32_t *blk = runs + lo;
-    auto slot_of = [&](uint32_t v) { return (v * 0x9e3779b1u) >> (32 - slot_bits); };
+    auto hash = [](uint32_t v, int bits) { return (v * 0x9e3779b1u) >> (32 - bits); };
     for (int i = threadIdx.x; i < slots; i += kTagThreads) H[i] = 0ull;
-    if (threadIdx.x == 0) ndup = 0;
+    for (int i = threadIdx.x; i < kTagDupSlots; i += kTagThreads) {
+        D[i] = 0ull;
+        dfill[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        ndist = 0;
+        nlist = 0;
+        bad = 0;
+    }
     __syncthreads();
+    // the sampled keys: once-occurring ones into H; repeated ones into D, with
+    // their occurrence counts (the run of equal keys around r)
     for (int64_t j = 1 + threadIdx.x; j <= js; j += kTagThreads) {
         const int64_t r = j * x - 1;
         const uint32_t v = blk[r];
         sphi[k * s + (j - 1)] = v;
-        // the key occurs once unless a neighbour holds it too
-        const bool single = (r == 0 || blk[r - 1] != v) && (r + 1 == len || blk[r + 1] != v);
-        if (single) {
+        if ((r == 0 || blk[r - 1] != v) && (r + 1 == len || blk[r + 1] != v)) {
             const unsigned long long e = (unsigned long long)v << 32 | (uint32_t)j;
-            uint32_t h = slot_of(v);
+            uint32_t h = hash(v, slot_bits);
             for (int probe = 0; probe < slots; ++probe, h = (h + 1) & (slots - 1))
                 if (atomicCAS(&H[h], 0ull, e) == 0ull) break;
-        } else {
-            const uint32_t at = atomicAdd(&ndup, 1u);
-            if (at < kTagDupMax) dup[at] = (uint32_t)j;
+            continue;
         }
-    }
-    __syncthreads();
-    if (ndup > kTagDupMax) {  // uniform
-        if (threadIdx.x == 0) retry[k] = 1u;
-        return;
-    }
-    // keys that occur once: one pass over the block's input
-    for (int64_t t = threadIdx.x; t < len; t += kTagThreads) {
-        const uint32_t u = (uint32_t)KeyTraits<DT>::phi(keys[lo + t]);
-        uint32_t h = slot_of(u);
-        for (int probe = 0; probe < slots; ++probe, h = (h + 1) & (slots - 1)) {
-            const unsigned long long e = H[h];
-            if (e == 0ull) break;
-            if ((uint32_t)(e >> 32) == u) {
-                stag[k * s + ((uint32_t)e - 1)] = (uint32_t)(lo + t);
-                break;
+        uint32_t h = hash(v, kTagDupBits);
+        for (int probe = 0; probe < kTagDupSlots; ++probe, h = (h + 1) & (kTagDupSlots - 1)) {
+            const unsigned long long cur = D[h];
+            if (cur != 0ull && (uint32_t)(cur >> 32) == v) break;  // another sampled rank of the same key
+            if (cur == 0ull) {
+                const uint32_t d = atomicAdd(&ndist, 1u);
+                if (d >= kTagDupSlots / 2) {
+                    bad = 1;
+                    break;
+                }
+                const unsigned long long want = (unsigned long long)v << 32 | (d + 1);
+                const unsigned long long old = atomicCAS(&D[h], 0ull, want);
+                if (old == 0ull) {
+                    int64_t a = 0, b = r;  // the run of v: [a, c)
+                    while (a < b) {
+                        const int64_t mid = (a + b) >> 1;
+                        if (blk[mid] < v) a = mid + 1;
+                        else b = mid;
+                    }
+                    int64_t lo2 = r, c = len;
+                    while (lo2 < c) {
+                        const int64_t mid = (lo2 + c) >> 1;
+                        if (blk[mid] <= v) lo2 = mid + 1;
+                        else c = mid;
+                    }
+                    const uint32_t cnt = (uint32_t)(c - a);
+                    dcount[d] = cnt;
+                    const uint32_t at = atomicAdd(&nlist, cnt);
+                    if (cnt > (uint32_t)kTagRunMax || at + cnt > (uint32_t)kTagListMax) bad = 1;
+                    dstart[d] = at;
+                    break;
+                }
+                if ((uint32_t)(old >> 32) == v) break;
+                // the slot went to another key: probe on (d stays unused)
             }
         }
     }
-    // repeated keys: the o-th occurrence in input order, one warp each
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t d = warp; d < ndup; d += kTagThreads / 32) {
-        const int64_t j = dup[d], r = j * x - 1;
+    __syncthreads();
+    if (bad) {  // uniform
+        if (threadIdx.x == 0) retry[k] = 1u;
+        return;
+    }
+    const bool any_dup = ndist > 0;
+    // one pass over the block's input, kTagAhead keys per thread in flight
+    for (int64_t t0 = 0; t0 < len; t0 += (int64_t)kTagThreads * kTagAhead) {
+        uint32_t u[kTagAhead];
+#pragma unroll
+        for (int q = 0; q < kTagAhead; ++q) {
+            const int64_t t = t0 + q * kTagThreads + threadIdx.x;
+            u[q] = t < len ? (uint32_t)KeyTraits<DT>::phi(keys[lo + t]) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < kTagAhead; ++q) {
+            const int64_t t = t0 + q * kTagThreads + threadIdx.x;
+            if (t >= len) continue;
+            uint32_t h = hash(u[q], slot_bits);
+            for (int probe = 0; probe < slots; ++probe, h = (h + 1) & (slots - 1)) {
+                const unsigned long long e = H[h];
+                if (e == 0ull) break;
+                if ((uint32_t)(e >> 32) == u[q]) {
+                    stag[k * s + ((uint32_t)e - 1)] = (uint32_t)(lo + t);
+                    break;
+                }
+            }
+            if (any_dup) {
+                uint32_t g = hash(u[q], kTagDupBits);
+                for (int probe = 0; probe < kTagDupSlots; ++probe, g = (g + 1) & (kTagDupSlots - 1)) {
+                    const unsigned long long e = D[g];
+                    if (e == 0ull) break;
+                    if ((uint32_t)(e >> 32) == u[q]) {
+                        const uint32_t d = (uint32_t)e - 1;
+                        const uint32_t at = atomicAdd(&dfill[d], 1u);
+                        if (at < dcount[d]) list[dstart[d] + at] = (uint32_t)t;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    if (!any_dup) return;
+    __syncthreads();
+    // repeated keys: the o-th smallest of the gathered positions
+    for (int64_t j = 1 + threadIdx.x; j <= js; j += kTagThreads) {
+        const int64_t r = j * x - 1;
         const uint32_t v = blk[r];
-        int64_t a = 0, b = r;
+        if ((r == 0 || blk[r - 1] != v) && (r + 1 == len || blk[r + 1] != v)) continue;
+        uint32_t g = hash(v, kTagDupBits), d = 0;
+        for (int probe = 0; probe < kTagDupSlots; ++probe, g = (g + 1) & (kTagDupSlots - 1)) {
+            const unsigned long long e = D[g];
+            if (e == 0ull) break;
+            if ((uint32_t)(e >> 32) == v) {
+                d = (uint32_t)e - 1;
+                break;
+            }
+        }
+        int64_t a = 0, b = r;  // the first rank of v
         while (a < b) {
             const int64_t mid = (a + b) >> 1;
             if (blk[mid] < v) a = mid + 1;
             else b = mid;
         }
-        uint32_t o = (uint32_t)(r - a);
-        for (int64_t base = 0; base < len; base += 32) {
-            const int64_t t = base + lane;
-            const bool eq = t < len && (uint32_t)KeyTraits<DT>::phi(keys[lo + t]) == v;
-            const uint32_t bal = __ballot_sync(0xffffffffu, eq);
-            const uint32_t c = (uint32_t)__popc(bal);
-            if (o < c) {
-                uint32_t bits = bal;
-                for (uint32_t q = 0; q < o; ++q) bits &= bits - 1;  // drop the o lowest
-                if (lane == 0) stag[k * s + (j - 1)] = (uint32_t)(lo + base + __ffs(bits) - 1);
-                break;
-            }
-            o -= c;
+        const uint32_t o = (uint32_t)(r - a), c = dcount[d], *L = list + dstart[d];
+        uint32_t tag = 0;
+        for (uint32_t i = 0; i < c; ++i) {  // the position with exactly o smaller ones
+            uint32_t below = 0;
+            for (uint32_t q = 0; q < c; ++q) below += L[q] < L[i];
+            if (below == o) tag = L[i];
         }
+        stag[k * s + (j - 1)] = (uint32_t)(lo + tag);
     }
 }
 

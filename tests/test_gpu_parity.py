@@ -139,6 +139,22 @@ def test_gmm_f64_random_small_sample():
     assert_same(gpu, ref)
 
 
+@pytest.mark.parametrize("values", [1 << 22, 1 << 17, 1 << 31], ids=["some_repeats", "many_repeats", "distinct"])
+@pytest.mark.parametrize("dt", [np.int32, np.uint32, np.float32])
+def test_regular_block_counting_sort_and_tags(values, dt):
+    """Regular sampling of keys without payloads sorts the blocks by the
+    counting sort and recovers the sampled keys' tags: keys that occur once,
+    keys repeated a few times in a block (their o-th input occurrence), and
+    blocks with so many repeats that they go to the stable block sort."""
+    n, p = 1 << 20, 16
+    rng = np.random.default_rng(values % 1000 + 7)
+    raw = rng.integers(0, values, n)
+    keys = (raw.astype(np.float32) - values / 2) if dt == np.float32 else raw.astype(dt)
+    ref = ref_sort(keys, p, 1024, 0, oracle.REGULAR, 0)
+    gpu = run_gpu(keys, p, 1024, 0, oracle.REGULAR, 0)
+    assert_same(gpu, ref)
+
+
 @pytest.mark.parametrize("refine", [1, 2, 4])
 def test_f64_sub_buckets_above_the_two_per_sm_clusters(refine):
     """8-byte keys without payloads, few samples per bucket (s = 16): the
