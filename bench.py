@@ -120,7 +120,7 @@ COMPARE = {"tree": ("tree", dict(classify=0)), "sort": ("bucket_sort_final_step"
 # (bytes per key, source hash, payloads) of each capture; the segment copy's
 # from the 2^26-pair Zipf capture (4096 buckets of 16-key segments, as at 2^28)
 NCU_TRAFFIC = {"route_keys_kernel": ((271.608576e6 + 223.674880e6) / (1 << 26), "8baca4c618da453f", False),
-               "bucket_keys32_kernel": ((537.311488e6 + 487.655424e6) / (1 << 27), "ceb023d4ec9e106a", False),
+               "bucket_keys32_kernel": ((537.560320e6 + 488.348416e6) / (1 << 27), "5e6c3051540be3c1", False),
                "segment_copy_kernel": ((613.273600e6 + 498.500864e6) / (1 << 26), "cefd083be8a0bc0e", True)}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "segment_copy_kernel": ["paper_1408_6729_gb300/csrc/merge.cu"],
@@ -559,7 +559,10 @@ def report(args, wl, name, world, n, p, plan, st, per_step, elapsed_ms, e2e_ms, 
     # (kernel, algorithmic bytes) of every phase that moves all the keys
     model = {}
     if wl["sampling"] == 0:  # the block sort reads every key (and writes the sorted blocks when it keeps them)
-        model["sample"] = (wl.get("block_sort_kernel", "run_sample_keys_kernel"), n * (2 * kb if keep else key_bytes))
+        # keys without payloads in whole 16-byte groups: the counting sort (and the tag kernel)
+        counting = keep and not wl["pairs"] and n % 4 == 0 and -(-n // plan.R) % 4 == 0
+        kern0 = "run_sample_count_kernel" if counting else "run_sample_keys_kernel"
+        model["sample"] = (wl.get("block_sort_kernel", kern0), n * (2 * kb if keep else key_bytes))
     if merge:
         model["bucket_sort"] = ("merge_bucket_kernel", n * 2 * kb)
     else:
