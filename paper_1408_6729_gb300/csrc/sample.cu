@@ -433,6 +433,10 @@ run_sample_tags_kernel(const uint32_t *__restrict__ keys, const uint32_t *__rest
 constexpr int kLowCardThreads = 1024, kLowCardMax = 256, kLowCardSlots = 512;
 constexpr int kLowCardWarps = kLowCardThreads / 32;
 constexpr size_t kLowCardSmem = sizeof(uint32_t) * kLowCardWarps * kLowCardSlots;  // per-warp counts
+// blocks of at most kLowCardStashMax keys keep every key's slot from the first
+// pass (16 bits each), so the second pass neither reloads nor hashes the keys
+constexpr int64_t kLowCardStashMax = 65536;
+static size_t lowcard_smem(int64_t m) { return kLowCardSmem + (m <= kLowCardStashMax ? 2 * (size_t)m : 0); }
 template <int DT>
 __global__ void __launch_bounds__(kLowCardThreads, 1)
 run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, int64_t n, int64_t m, int64_t s,
@@ -443,6 +447,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     static_assert(sizeof(K) == 4, "32-bit keys");
     constexpr int T = kLowCardThreads, W = kLowCardWarps, NS = kLowCardSlots;
     extern __shared__ __align__(16) uint32_t wcnt[];       // [W][NS]: keys per slot in warp w's segment
+    uint16_t *sid16 = reinterpret_cast<uint16_t *>(wcnt + kLowCardWarps * kLowCardSlots);  // slot of each key
     __shared__ unsigned long long slot[NS];                 // (1 << 32) | phi, 0 = empty
     __shared__ uint32_t start[NS];                          // sorted start of the slot's value
     __shared__ uint32_t vals[kLowCardMax], sid[kLowCardMax], rank_of[kLowCardMax], tot_sorted[kLowCardMax];
@@ -451,6 +456,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     __shared__ int ndistinct, overflow;
     const int64_t k = blockIdx.x;
     if (retry[k] == 0) return;  // sorted by the keys-only block sort
+    const bool stash = m <= kLowCardStashMax;
     const uint32_t xx = (uint32_t)x;
     const int64_t lo = k * m;
     const int64_t len = lo < n ? imin64(m, n - lo) : 0;
@@ -515,6 +521,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
                 const uint32_t f = fa[u];
                 const int h = find(f, true);
                 const uint32_t peers = __match_any_sync(act, f);
+                if (stash) sid16[e0 + u * 32 + lane] = (uint16_t)max(h, 0);
                 if (h < 0) overflow = 1;
                 else if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);  // this warp's own counts
             }
@@ -588,23 +595,36 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
         }
     }
     // pass 2: in position order, sorted rank = start + earlier segments + earlier here
+    const float inv_x = 1.0f / (float)xx;
     for (int64_t e0 = seg0; e0 < seg1; e0 += 32 * kAhead) {
-        load_ahead(e0);
+        if (!stash) load_ahead(e0);
 #pragma unroll
         for (int u = 0; u < kAhead; ++u) {
             const int64_t e = e0 + u * 32 + lane;
             const bool ok = e < seg1;
             const uint32_t act = __ballot_sync(0xffffffffu, ok);
             if (ok) {
-                const uint32_t f = fa[u];
-                const int h = max(0, find(f, false));  // present: every key was counted
-                const uint32_t peers = __match_any_sync(act, f);
+                int h;
+                uint32_t f;
+                if (stash) {
+                    h = sid16[e];
+                    f = (uint32_t)slot[h];
+                } else {
+                    f = fa[u];
+                    h = max(0, find(f, false));  // present: every key was counted
+                }
+                const uint32_t peers = __match_any_sync(act, (uint32_t)h);
                 const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
                 __syncwarp(act);
                 if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
                 if (runs_val) runs_val[lo + g1 - 1] = vals_in[lo + e];  // payloads at their ranks
-                if (g1 % xx == 0) {
-                    const int64_t j = g1 / xx;
+                // j = g1 / x when x divides g1 (the quotient from a float
+                // estimate, corrected by one either way)
+                uint32_t j = (uint32_t)((float)g1 * inv_x);
+                int64_t rem = (int64_t)g1 - (int64_t)j * xx;
+                if (rem >= (int64_t)xx) { ++j; rem -= xx; }
+                if (rem < 0) { --j; rem += xx; }
+                if (rem == 0) {
                     sphi[k * s + (j - 1)] = (K)f;
                     stag[k * s + (j - 1)] = (uint32_t)(lo + e);
                 }
@@ -1372,9 +1392,9 @@ template <int DT> static cudaError_t launch_sample_t(const Ctx &c) {
         if (e != cudaSuccess) return e;
         if (only) {  // blocks of few distinct keys, before the stable sort
             e = cudaFuncSetAttribute(run_sample_lowcard_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLowCardSmem);
+                                     (int)lowcard_smem(p.m));
             if (e != cudaSuccess) return e;
-            run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, kLowCardSmem, c.stream>>>(
+            run_sample_lowcard_kernel<DT><<<(unsigned)p.R, kLowCardThreads, lowcard_smem(p.m), c.stream>>>(
                 (const K *)c.keys_in, p.n, p.m, p.s, p.x, (K *)c.ly.sphi[0], c.ly.stag[0], c.ly.run_retry,
                 p.keep_runs ? (K *)c.ly.runs : nullptr, c.vals_in, p.keep_runs && p.pairs ? c.ly.runs_val : nullptr);
             e = cudaGetLastError();
