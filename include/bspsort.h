@@ -6,9 +6,14 @@
  *   Sort_Det_BSP  (Fig. 1, Sec. 5.1)  -- regular (deterministic) oversampling
  *   Sort_IRan_BSP (Fig. 3, Sec. 5.2)  -- random oversampling
  * with the duplicate-key handling of Sec. 5.1.1.  On one GPU the p BSP
- * processors become p buckets: every key is classified against the p-1
- * splitters (Fig. 2 step 9), routed once through HBM in input order
- * (Fig. 1 step 11), and each bucket is sorted in on-chip memory (Fig. 2 step 12).
+ * processors become p buckets.  With random oversampling every key is
+ * classified against the p-1 splitters (Fig. 2 step 9) and routed once
+ * through HBM in input order (Fig. 1 step 11).  With regular oversampling of
+ * 4-byte keys the blocks sorted for the sample are kept, every splitter is
+ * located in every sorted block (Fig. 1 step 9) and each bucket's segments
+ * are copied in block order (steps 10-11).  Each bucket is then sorted in
+ * on-chip memory (Fig. 2 step 12), or -- BSPS_FINAL_MERGE -- its sorted
+ * segments are merged (Fig. 1 step 12).
  *
  * Conventions shared by every entry point
  *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
