@@ -148,6 +148,8 @@ struct MlpOpt {
     float best[kParams], grad[kParams], start[kParams];
     float best_loss, eta;
 };
+// the descent state, then (16-byte aligned) the scratch of the evaluation form
+static size_t mlp_scratch_offset() { return (sizeof(MlpOpt) + 15) & ~size_t(15); }
 
 // Sums the G partial gradients and losses of the current parameters; keeps
 // them as the best if their loss is the lowest so far (the step size grows)
@@ -205,27 +207,38 @@ __global__ void __launch_bounds__(1024) mlp_descent_kernel(float *params, const 
 }
 
 // The piecewise-linear form of the network `params` (see MlpTables), in
-// double.  Warp k takes layer 1's interval k (between its sorted knots k-1
-// and k), lane i layer 2's unit i: the lane forms the unit's affine
-// pre-activation there and its zero crossing; the crossings inside the
-// interval cut it into pieces, and for every piece the warp sums the active
-// units' slopes and values at the piece's anchor.  The pieces of all
-// intervals are then written in order.  A network of more than kMlpPieces
-// pieces is replaced by `fallback` (the spline start, at most 33 pieces),
-// when given.
-constexpr int kTablesThreads = 1024;
-__global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const float *params_in, const float *fallback,
-                                                                    const MlpNorm *norm, MlpTables *T) {
+// double, in two kernels.  mlp_pieces_kernel: one warp (CTA) per layer-1
+// interval k (between its sorted knots k-1 and k) of each parameter set --
+// the trained network and the `fallback` -- lane i taking layer 2's unit i:
+// the lane forms the unit's affine pre-activation there and its zero
+// crossing; the crossings inside the interval cut it into pieces, and for
+// every piece the warp sums the active units' slopes and values at the
+// piece's anchor.  (One warp per interval on separate SMs: the double
+// arithmetic of all intervals on one SM took 0.12 ms.)  mlp_tables_kernel
+// then writes the pieces of all intervals in order; a network of more than
+// kMlpPieces pieces is replaced by the fallback (the spline start, at most 33
+// pieces), when given.
+struct MlpPieceSet {
+    double knots[kH];
+    int nk;
+    int n[kH + 1];
+    float x[kH + 1][kH + 1], y[kH + 1][kH + 1], s[kH + 1][kH + 1];
+};
+struct MlpPieceScratch {
+    MlpPieceSet set[2];  // the trained parameters, the fallback
+};
+
+__global__ void __launch_bounds__(32) mlp_pieces_kernel(const float *params_in, const float *fallback,
+                                                        MlpPieceScratch *scr) {
+    const int which = blockIdx.x / (kH + 1), k = blockIdx.x % (kH + 1), lane = threadIdx.x;
+    const float *params = which == 0 ? params_in : fallback;
+    if (!params) return;
+    MlpPieceSet &S = scr->set[which];
     __shared__ double knots[kH];
-    __shared__ double cutd[kH + 1][kH + 1];
+    __shared__ double cutd[kH + 1];
     __shared__ int nk;
-    __shared__ float s_x[kMlpPiecesAll], s_y[kMlpPiecesAll], s_s[kMlpPiecesAll];
-    __shared__ int s_n[kH + 1], s_off[kH + 2];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const double INF = __longlong_as_double(0x7ff0000000000000ll);
-    const float *params = params_in;
-  again:
-    if (t == 0) {
+    if (lane == 0) {
         int c = 0;
         for (int j = 0; j < kH; ++j) {
             const double w = params[kW1 + j];
@@ -237,65 +250,99 @@ __global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const float 
             }
         }
         nk = c;
+        if (k == 0) {
+            S.nk = c;
+            for (int j = 0; j < c; ++j) S.knots[j] = knots[j];
+        }
+    }
+    __syncwarp();
+    const int c = nk;
+    if (k > c) {
+        if (lane == 0) S.n[k] = 0;
+        return;
+    }
+    const double w3 = params[kW3 + lane];
+    const double lo = k == 0 ? -INF : knots[k - 1], hi = k == c ? INF : knots[k];
+    // a point inside the interval decides which layer-1 units are on
+    double xm = 0.0;
+    if (c > 0) xm = k == 0 ? knots[0] - 1.0 : (k == c ? knots[c - 1] + 1.0 : 0.5 * (lo + hi));
+    double A = params[kB2 + lane], B = 0.0;  // unit `lane` of layer 2: A + B x here
+    for (int j = 0; j < kH; ++j) {
+        const double w1 = params[kW1 + j], b1 = params[kB1 + j];
+        if (w1 * xm + b1 > 0.0) {
+            const double w2 = params[kW2 + lane * kH + j];
+            A += w2 * b1;
+            B += w2 * w1;
+        }
+    }
+    // its zero crossing, when inside the interval, ranked among the others
+    const double z = B != 0.0 ? -A / B : 0.0;
+    const bool in = B != 0.0 && z > lo && z < hi;
+    const uint32_t valid = __ballot_sync(0xffffffffu, in);
+    int rank = 0;
+    for (int q = 0; q < 32; ++q) {
+        const double zq = __shfl_sync(0xffffffffu, z, q);
+        rank += ((valid >> q) & 1u) && (zq < z || (zq == z && q < lane));
+    }
+    if (in) cutd[rank] = z;
+    __syncwarp();
+    const int m = __popc(valid);
+    // piece r of the interval: [left_r, right_r)
+    for (int r = 0; r <= m; ++r) {
+        const double left = r == 0 ? lo : cutd[r - 1], right = r == m ? hi : cutd[r];
+        double mid, anchor;
+        if (left == -INF && right == INF) { mid = 0.0; anchor = 0.0; }
+        else if (left == -INF) { mid = right - 1.0; anchor = right; }
+        else if (right == INF) { mid = left + 1.0; anchor = left; }
+        else { mid = 0.5 * (left + right); anchor = left; }
+        const bool on = A + B * mid > 0.0;
+        double y = on ? w3 * (A + B * anchor) : 0.0, sl = on ? w3 * B : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        }
+        if (lane == 0) {
+            y += params[kB3];
+            // a finite piece over which the network falls by less than
+            // 2^-30 (far below the output's float resolution and its
+            // index cells) is taken as flat
+            if (sl < 0.0 && left != -INF && right != INF && -sl * (right - left) < 9.313225746154785e-10) sl = 0.0;
+            S.x[k][r] = (float)anchor;
+            S.y[k][r] = (float)y;
+            S.s[k][r] = (float)sl;
+        }
+    }
+    if (lane == 0) S.n[k] = m + 1;
+}
+
+constexpr int kTablesThreads = 1024;
+__global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const MlpPieceScratch *scr, int has_fallback,
+                                                                    const MlpNorm *norm, MlpTables *T) {
+    __shared__ float s_x[kMlpPiecesAll], s_y[kMlpPiecesAll], s_s[kMlpPiecesAll];
+    __shared__ int s_n[kH + 1], s_off[kH + 2];
+    __shared__ double knots[kH];
+    __shared__ int use;
+    const int t = threadIdx.x;
+    if (t == 0) {  // the trained network, unless it has too many pieces and a fallback exists
+        int o = 0;
+        const MlpPieceSet &S0 = scr->set[0];
+        for (int k = 0; k <= S0.nk; ++k) o += S0.n[k];
+        use = (o > kMlpPieces && has_fallback) ? 1 : 0;
     }
     __syncthreads();
-    const int c = nk;
-    const double w3 = params[kW3 + lane];
-    for (int k = warp; k <= c; k += kTablesThreads / 32) {
-        const double lo = k == 0 ? -INF : knots[k - 1], hi = k == c ? INF : knots[k];
-        // a point inside the interval decides which layer-1 units are on
-        double xm = 0.0;
-        if (c > 0) xm = k == 0 ? knots[0] - 1.0 : (k == c ? knots[c - 1] + 1.0 : 0.5 * (lo + hi));
-        double A = params[kB2 + lane], B = 0.0;  // unit `lane` of layer 2: A + B x here
-        for (int j = 0; j < kH; ++j) {
-            const double w1 = params[kW1 + j], b1 = params[kB1 + j];
-            if (w1 * xm + b1 > 0.0) {
-                const double w2 = params[kW2 + lane * kH + j];
-                A += w2 * b1;
-                B += w2 * w1;
-            }
+    const MlpPieceSet &S = scr->set[use];
+    const int c = S.nk;
+    for (int i = t; i < (kH + 1) * (kH + 1); i += kTablesThreads) {
+        const int k = i / (kH + 1), r = i % (kH + 1);
+        if (k <= c && r < S.n[k]) {
+            s_x[i] = S.x[k][r];
+            s_y[i] = S.y[k][r];
+            s_s[i] = S.s[k][r];
         }
-        // its zero crossing, when inside the interval, ranked among the others
-        const double z = B != 0.0 ? -A / B : 0.0;
-        const bool in = B != 0.0 && z > lo && z < hi;
-        const uint32_t valid = __ballot_sync(0xffffffffu, in);
-        int rank = 0;
-        for (int q = 0; q < 32; ++q) {
-            const double zq = __shfl_sync(0xffffffffu, z, q);
-            rank += ((valid >> q) & 1u) && (zq < z || (zq == z && q < lane));
-        }
-        if (in) cutd[k][rank] = z;
-        __syncwarp();
-        const int m = __popc(valid);
-        // piece r of the interval: [left_r, right_r)
-        for (int r = 0; r <= m; ++r) {
-            const double left = r == 0 ? lo : cutd[k][r - 1], right = r == m ? hi : cutd[k][r];
-            double mid, anchor;
-            if (left == -INF && right == INF) { mid = 0.0; anchor = 0.0; }
-            else if (left == -INF) { mid = right - 1.0; anchor = right; }
-            else if (right == INF) { mid = left + 1.0; anchor = left; }
-            else { mid = 0.5 * (left + right); anchor = left; }
-            const bool on = A + B * mid > 0.0;
-            double y = on ? w3 * (A + B * anchor) : 0.0, sl = on ? w3 * B : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                y += __shfl_xor_sync(0xffffffffu, y, o);
-                sl += __shfl_xor_sync(0xffffffffu, sl, o);
-            }
-            if (lane == 0) {
-                y += params[kB3];
-                // a finite piece over which the network falls by less than
-                // 2^-30 (far below the output's float resolution and its
-                // index cells) is taken as flat
-                if (sl < 0.0 && left != -INF && right != INF && -sl * (right - left) < 9.313225746154785e-10) sl = 0.0;
-                const int q = k * (kH + 1) + r;
-                s_x[q] = (float)anchor;
-                s_y[q] = (float)y;
-                s_s[q] = (float)sl;
-            }
-        }
-        if (lane == 0) s_n[k] = m + 1;
     }
+    for (int k = t; k <= c; k += kTablesThreads) s_n[k] = S.n[k];
+    for (int j = t; j < c; j += kTablesThreads) knots[j] = S.knots[j];
     __syncthreads();
     if (t == 0) {
         int o = 0;
@@ -303,11 +350,6 @@ __global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const float 
         s_off[c + 1] = o;
     }
     __syncthreads();
-    if (s_off[c + 1] > kMlpPieces && fallback && params != fallback) {  // uniform
-        params = fallback;
-        __syncthreads();
-        goto again;
-    }
     if (t == 0) {
         const int o = min(s_off[c + 1], kMlpPieces);
         int npad = 1;
@@ -348,6 +390,14 @@ __global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const float 
     __syncthreads();
     const int np = min(s_off[c + 1], kMlpPieces);
     for (int q = np - 1 + t; q < kMlpCutsPad; q += kTablesThreads) T->cut[q] = __int_as_float(0x7f800000);
+}
+
+// both kernels of the evaluation form
+static cudaError_t launch_tables(const float *params, const float *fallback, const MlpNorm *norm, MlpTables *T,
+                                 MlpPieceScratch *scr, cudaStream_t st) {
+    mlp_pieces_kernel<<<2 * (kH + 1), 32, 0, st>>>(params, fallback, scr);
+    mlp_tables_kernel<<<1, kTablesThreads, 0, st>>>(scr, fallback != nullptr, norm, T);
+    return cudaGetLastError();
 }
 
 // The network's output for every splitter (S_{j+1} at index j).
@@ -546,7 +596,11 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     }
     // the trained network in its evaluation form, and the index over the
     // splitters' outputs
-    mlp_tables_kernel<<<1, kTablesThreads, 0, c.stream>>>(c.ly.mlp_params, opt->start, c.ly.mlp_norm, c.ly.mlp_tables);
+    cudaError_t e0 = launch_tables(c.ly.mlp_params, opt->start, c.ly.mlp_norm, c.ly.mlp_tables,
+                                   reinterpret_cast<MlpPieceScratch *>(reinterpret_cast<unsigned char *>(c.ly.mlp_opt) +
+                                                                       mlp_scratch_offset()),
+                                   c.stream);
+    if (e0 != cudaSuccess) return e0;
     const int64_t nsplit = p.P - 1;
     if (nsplit > 0)
         mlp_ysplit_kernel<DT><<<(unsigned)((nsplit + 255) / 256), 256, 0, c.stream>>>(
@@ -559,8 +613,8 @@ template <int DT> static cudaError_t launch_mlp_train_t(const Ctx &c) {
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-int mlp_train_kernels() { return 2 + 2 * (kMlpSteps + 1) + 3; }
-size_t mlp_opt_bytes() { return sizeof(MlpOpt); }
+int mlp_train_kernels() { return 2 + 2 * (kMlpSteps + 1) + 4; }
+size_t mlp_opt_bytes() { return mlp_scratch_offset() + sizeof(MlpPieceScratch); }
 
 cudaError_t launch_mlp_train(const Ctx &c) {
     switch (c.pl.dtype) {
@@ -578,7 +632,8 @@ using namespace bsps;
 extern "C" int bsps_mlp_workspace_size(int64_t m, size_t *bytes) {
     if (!bytes || m < 0) return BSPS_ERR_INVALID_ARG;
     const int64_t G = (m + kMlpThreads - 1) / kMlpThreads;
-    *bytes = std::max((size_t)std::max<int64_t>(G, 1) * (kParams + 1) * sizeof(float), sizeof(MlpTables)) + 256;
+    *bytes = std::max((size_t)std::max<int64_t>(G, 1) * (kParams + 1) * sizeof(float),
+                      ((sizeof(MlpTables) + 15) & ~size_t(15)) + sizeof(MlpPieceScratch)) + 256;
     return BSPS_OK;
 }
 
@@ -598,10 +653,15 @@ extern "C" int bsps_mlp_loss_grad(const float *d_params, const float *d_x, const
 extern "C" int bsps_mlp_predict(const float *d_params, const float *d_x, int64_t m, float *d_y, void *d_ws,
                                 size_t ws_bytes, void *stream) {
     if (m < 0 || !d_params || (m > 0 && (!d_x || !d_y))) return BSPS_ERR_INVALID_ARG;
-    if (!d_ws || ws_bytes < sizeof(MlpTables) || ((uintptr_t)d_ws & 15) != 0) return BSPS_ERR_WORKSPACE_TOO_SMALL;
+    const size_t toff = (sizeof(MlpTables) + 15) & ~size_t(15);
+    if (!d_ws || ws_bytes < toff + sizeof(MlpPieceScratch) || ((uintptr_t)d_ws & 15) != 0)
+        return BSPS_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
     MlpTables *T = (MlpTables *)d_ws;
-    mlp_tables_kernel<<<1, kTablesThreads, 0, s>>>(d_params, nullptr, nullptr, T);
+    if (launch_tables(d_params, nullptr, nullptr, T,
+                      reinterpret_cast<MlpPieceScratch *>(reinterpret_cast<unsigned char *>(d_ws) + toff),
+                      s) != cudaSuccess)
+        return BSPS_ERR_CUDA;
     if (m > 0) mlp_predict_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(T, d_x, m, d_y);
     return cudaGetLastError() == cudaSuccess ? BSPS_OK : BSPS_ERR_CUDA;
 }
