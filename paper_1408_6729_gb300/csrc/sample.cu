@@ -583,15 +583,23 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     __syncthreads();
     if (runs) {
         // the sorted block's keys: value of rank r over [start_r, start_r+1),
-        // written in position order
-        for (int64_t t = tid; t < len; t += T) {
-            int l = 0, h = nd - 1;  // the last rank starting at or before t
+        // written in position order.  Warp w writes positions [w*len/W,
+        // (w+1)*len/W), 32 consecutive ones at a time; each lane finds the
+        // rank of its first position and then walks forward.
+        const int64_t p0 = (int64_t)warp * len / W, p1 = (int64_t)(warp + 1) * len / W;
+        int r = 0;
+        if (p0 + lane < p1) {
+            int l = 0, h = nd - 1;  // the last rank starting at or before the position
             while (l < h) {
                 const int mid = (l + h + 1) >> 1;
-                if (tot_sorted[mid] <= (uint32_t)t) l = mid;
+                if (tot_sorted[mid] <= (uint32_t)(p0 + lane)) l = mid;
                 else h = mid - 1;
             }
-            runs[lo + t] = (K)val_of_rank[l];
+            r = l;
+        }
+        for (int64_t t = p0 + lane; t < p1; t += 32) {
+            while (r + 1 < nd && tot_sorted[r + 1] <= (uint32_t)t) ++r;
+            runs[lo + t] = (K)val_of_rank[r];
         }
     }
     // pass 2: in position order, sorted rank = start + earlier segments + earlier here
