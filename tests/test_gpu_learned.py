@@ -99,6 +99,18 @@ def test_learned_sort_is_exact(name, make, p, s):
     assert_same(gpu, ref)
 
 
+@pytest.mark.parametrize("pairs", [False, True], ids=["keys", "pairs"])
+def test_learned_with_regular_sampling(pairs):
+    """Regular oversampling with the learned classifier: the network is
+    trained on the regular sample and every key classified through it (the
+    classification route); output, sizes and per-key buckets as the oracle's."""
+    keys = gen.gmm(1 << 20, seed=11).astype(np.float32)
+    vals = np.arange(keys.shape[0], dtype=np.uint32) if pairs else None
+    ref = oracle.sort(keys, 64, 0, 0, oracle.REGULAR, 0, vals=vals, want_bucket_of=True)
+    gpu = run_gpu(keys, 64, 0, 0, oracle.REGULAR, 0, vals, classify=1)
+    assert_same(gpu, ref)
+
+
 def test_training_lowers_the_loss_and_the_index_finds_most_buckets():
     """Training moves every layer and keeps the lowest loss (never above the
     spline start's); the index over the network's output holds most keys'

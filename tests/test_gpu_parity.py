@@ -155,6 +155,20 @@ def test_regular_block_counting_sort_and_tags(values, dt):
     assert_same(gpu, ref)
 
 
+@pytest.mark.parametrize("name,make,p", [("uniform", lambda: gen.uniform(1 << 21, 256, 3), 256),
+                                         ("zipf", lambda: gen.zipf(1 << 21, seed=3), 64),
+                                         ("gmm_f64", lambda: gen.gmm(1 << 20, seed=3), 512)],
+                         ids=["uniform", "zipf", "gmm_f64"])
+def test_random_mode_against_sort_ran_bsp(name, make, p):
+    """Random oversampling on the GPU classifies every key and sorts every
+    bucket -- the shape of Sort_Ran_BSP (Fig. 2): its per-key buckets, sizes
+    and output equal the oracle's Fig. 2 run (as well as its Fig. 3 run)."""
+    keys = make()
+    ref = oracle.sort(keys, p, 0, 0, oracle.RANDOM, 5, want_bucket_of=True, variant=oracle.RAN)
+    gpu = run_gpu(keys, p, 0, 0, oracle.RANDOM, 5)
+    assert_same(gpu, ref)
+
+
 @pytest.mark.parametrize("refine", [1, 2, 4])
 def test_f64_sub_buckets_above_the_two_per_sm_clusters(refine):
     """8-byte keys without payloads, few samples per bucket (s = 16): the
