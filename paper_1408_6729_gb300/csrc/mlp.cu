@@ -390,25 +390,6 @@ __global__ void __launch_bounds__(kTablesThreads) mlp_tables_kernel(const MlpPie
     __syncthreads();
     const int np = min(s_off[c + 1], kMlpPieces);
     for (int q = np - 1 + t; q < kMlpCutsPad; q += kTablesThreads) T->cut[q] = __int_as_float(0x7f800000);
-    __syncthreads();
-    // the index over the cut points: kPlutCells cells over [first, last cut],
-    // each with the number of cuts at or below its left end
-    const float x0 = np > 1 ? T->cut[0] : 0.0f, x1 = np > 1 ? T->cut[np - 2] : 0.0f;
-    const float pinv = x1 > x0 ? (float)kPlutCells / (x1 - x0) : 0.0f;
-    if (t == 0) {
-        T->px0 = x0;
-        T->pinv = pinv;
-    }
-    for (int cc = t; cc < kPlutCells; cc += kTablesThreads) {
-        const float left = pinv > 0.0f ? x0 + (float)cc / pinv : x0;
-        int a = 0, b = max(np - 1, 0);  // cuts <= left among the real ones
-        while (a < b) {
-            const int mid = (a + b) >> 1;
-            if (T->cut[mid] <= left) a = mid + 1;
-            else b = mid;
-        }
-        T->plut[cc] = (uint16_t)a;
-    }
 }
 
 // both kernels of the evaluation form

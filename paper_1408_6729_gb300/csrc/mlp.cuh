@@ -72,7 +72,6 @@ constexpr int kYCells = 1 << kYCellBits;
 constexpr int kMlpPiecesAll = (kH + 1) * (kH + 1);  // at most 33 layer-1 intervals x 33 layer-2 pieces
 constexpr int kMlpPieces = 256;                // pieces kept (else the spline start, at most 33, is used)
 constexpr int kMlpCutsPad = kMlpPieces;        // cut points, padded to a power of two with +inf
-constexpr int kPlutCells = 512;                // cells of the index over the cut points
 struct MlpTables {
     float cut[kMlpCutsPad];    // ascending left ends of pieces 1 .. np-1, then +inf
     float4 piece[kMlpPieces];  // (x_p, y_p, s_p, y_{p+1}) of piece p = [cut[p-1], cut[p])
@@ -81,21 +80,12 @@ struct MlpTables {
     int32_t monotone;          // every slope >= 0: the evaluation is nondecreasing
     int32_t pad_;
     MlpNorm norm;
-    float px0, pinv;           // cell c of x: floor((x - px0) * pinv), clamped
-    uint16_t plut[kPlutCells]; // a first guess at the cut points <= x for x in cell c
 };
 
 __device__ __forceinline__ float mlp_eval(const MlpTables &T, float x) {
-    // p = number of cut points <= x among the first npad - 1 (+inf beyond the
-    // real ones): from the cell's guess, walked forward and back to the exact
-    // count (a NaN counts none)
+    // p = number of cut points <= x (a fixed-depth search)
     int p = 0;
-    if (x == x) {
-        const float u = fminf(fmaxf((x - T.px0) * T.pinv, 0.0f), (float)(kPlutCells - 1));
-        p = T.plut[(int)u];
-        while (p < T.npad - 1 && T.cut[p] <= x) ++p;
-        while (p > 0 && T.cut[p - 1] > x) --p;
-    }
+    for (int st = T.npad >> 1; st >= 1; st >>= 1) p += T.cut[p + st - 1] <= x ? st : 0;
     const float4 pc = T.piece[p];
     float y = fmaf(pc.z, x - pc.x, pc.y);
     if (T.monotone) {  // clamped to the piece's end values
