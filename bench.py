@@ -120,8 +120,8 @@ COMPARE = {"tree": ("tree", dict(classify=0)), "sort": ("bucket_sort_final_step"
 # (bytes per key, source hash, payloads) of each capture; the segment copy's
 # from the 2^26-pair Zipf capture (4096 buckets of 16-key segments, as at 2^28)
 NCU_TRAFFIC = {"route_keys_kernel": ((271.608576e6 + 223.674880e6) / (1 << 26), "8baca4c618da453f", False),
-               "bucket_keys32_kernel": ((537.560320e6 + 488.348416e6) / (1 << 27), "5e6c3051540be3c1", False),
-               "segment_copy_kernel": ((613.273600e6 + 498.500864e6) / (1 << 26), "cefd083be8a0bc0e", True)}
+               "bucket_keys32_kernel": ((537.268992e6 + 486.783232e6) / (1 << 27), "b2f4fe6e7d92e3af", False),
+               "segment_copy_kernel": ((617.909248e6 + 494.979328e6) / (1 << 26), "333c4e171f9cd65e", True)}
 KERNEL_SOURCE = {"route_kernel": ["paper_1408_6729_gb300/csrc/route.cu"],
                  "segment_copy_kernel": ["paper_1408_6729_gb300/csrc/merge.cu"],
                  "route_keys_kernel": ["paper_1408_6729_gb300/csrc/route_keys.cu",

@@ -36,6 +36,7 @@ template <typename K> struct BucketArgs {
     const int32_t *only_count;
     int64_t defer_above;      // tier 1: sub-buckets above this many keys are left to the larger tier 1
     int64_t take_above;       // larger tier 1: only sub-buckets above this many keys
+    int one_value_done;       // sub-buckets of one key value are already in the output
 };
 
 template <int DT, bool PAIRS, int CL, int ITEMS>
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kCopyThreads) bucket_copy_kernel(const BucketA
         const int64_t cnt = imin64(a.vsize[v], a.cap);
         if (cnt == 0) continue;
         if (v > 0 && v < a.P - 1 && a.vphi[v - 1] == a.vphi[v]) {
+            if (a.one_value_done) continue;  // the segment copy wrote it
             const K x = KeyTraits<DT>::inv(a.vphi[v]);
             K *out_k = a.out_keys + a.voff[v];
             uint32_t *out_v = a.out_vals + a.voff[v];
@@ -335,6 +337,7 @@ template <int DT, bool PAIRS> static cudaError_t launch_bucket_t(const Ctx &c) {
     a.only_count = nullptr;
     a.defer_above = INT64_MAX;
     a.take_above = 0;
+    a.one_value_done = c.pl.seg_route;
     constexpr int IT = PAIRS ? (sizeof(K) == 8 ? kPairItems64 : kPairItems32)
                              : (sizeof(K) == 8 ? kBucketItems64 : kBucketItems32);
     cudaError_t e = cudaSuccess;

@@ -406,19 +406,34 @@ __global__ void __launch_bounds__(kMergeThreads, PAIRS ? 1 : 2) merge_bucket_ker
 // ---------------------------------------------------------------------------
 constexpr int kSegThreads = 512, kSegItems = 8;
 
+struct SegCopyArgs {
+    const uint32_t *runs, *runs_val, *part, *vsize, *vphi;
+    const uint64_t *voff;
+    int64_t R, m, cap, P;
+    uint32_t *reg_keys, *reg_vals, *out_keys, *out_vals;
+    int dtype;
+    DevStatus *st;
+};
+
 template <bool PAIRS>
-__global__ void __launch_bounds__(kSegThreads) segment_copy_kernel(const uint32_t *__restrict__ runs,
-                                                                   const uint32_t *__restrict__ runs_val,
-                                                                   const uint32_t *__restrict__ part,
-                                                                   const uint32_t *__restrict__ vsize, int64_t R,
-                                                                   int64_t m, int64_t cap, uint32_t *reg_keys,
-                                                                   uint32_t *reg_vals, DevStatus *st) {
+__global__ void __launch_bounds__(kSegThreads) segment_copy_kernel(const SegCopyArgs a) {
     extern __shared__ __align__(16) uint32_t ssm[];
+    const int64_t R = a.R, m = a.m, cap = a.cap;
+    const uint32_t *__restrict__ runs = a.runs;
+    const uint32_t *__restrict__ runs_val = a.runs_val;
+    const uint32_t *part = a.part;
+    DevStatus *st = a.st;
     uint32_t *soff = ssm, *sst = ssm + R + 1;
     __shared__ uint32_t tmp[40];
     const int64_t v = blockIdx.x;
-    const uint32_t N = vsize[v];
+    const uint32_t N = a.vsize[v];
     if (N == 0 || N > cap) return;  // an overflow is already reported
+    // a sub-bucket between two equal splitters holds one key value, its
+    // segments in block order are its sorted order: keys only, the bucket
+    // sort writes it without reading; with payloads they go straight to the
+    // output here
+    const bool one = v > 0 && v < a.P - 1 && a.vphi[v - 1] == a.vphi[v];
+    if (one && !PAIRS) return;
     const uint32_t *rowa = part + v * R, *rowb = part + (v + 1) * R;
     for (int64_t k = threadIdx.x; k < R; k += kSegThreads) {
         const uint32_t x0 = rowa[k], x1 = rowb[k];
@@ -437,7 +452,9 @@ __global__ void __launch_bounds__(kSegThreads) segment_copy_kernel(const uint32_
     if (threadIdx.x == 0) soff[R] = N;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *dk = reg_keys + v * cap, *dv = PAIRS ? reg_vals + v * cap : nullptr;
+    uint32_t *dk = one ? a.out_keys + a.voff[v] : a.reg_keys + v * cap;
+    uint32_t *dv = PAIRS ? (one ? a.out_vals + a.voff[v] : a.reg_vals + v * cap) : nullptr;
+    const uint32_t key1 = one ? key_of_phi32(a.dtype, a.vphi[v]) : 0u;
     constexpr uint32_t RUN = 32 * kSegItems;
     for (uint32_t base = warp * RUN; base < N; base += (kSegThreads / 32) * RUN) {
         int64_t l = 0, h = R - 1;  // the last segment starting at or before base
@@ -462,7 +479,7 @@ __global__ void __launch_bounds__(kSegThreads) segment_copy_kernel(const uint32_
         for (int u = 0; u < kSegItems; ++u) {
             const uint32_t q = base + u * 32 + lane;
             if (q < N) {
-                dk[q] = kk[u];
+                dk[q] = one ? key1 : kk[u];
                 if constexpr (PAIRS) dv[q] = vv[u];
             }
         }
@@ -500,9 +517,24 @@ cudaError_t launch_segment_copy(const Ctx &c) {
     auto kern = p.pairs ? segment_copy_kernel<true> : segment_copy_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)p.P, kSegThreads, smem, c.stream>>>((const uint32_t *)c.ly.runs, c.ly.runs_val, c.ly.part,
-                                                         c.ly.vsize, p.R, p.m, p.cap, (uint32_t *)c.ly.reg_keys,
-                                                         c.ly.reg_vals, c.ly.status);
+    SegCopyArgs a;
+    a.runs = (const uint32_t *)c.ly.runs;
+    a.runs_val = c.ly.runs_val;
+    a.part = c.ly.part;
+    a.vsize = c.ly.vsize;
+    a.vphi = (const uint32_t *)c.ly.vphi;
+    a.voff = c.ly.voff;
+    a.R = p.R;
+    a.m = p.m;
+    a.cap = p.cap;
+    a.P = p.P;
+    a.reg_keys = (uint32_t *)c.ly.reg_keys;
+    a.reg_vals = c.ly.reg_vals;
+    a.out_keys = (uint32_t *)c.keys_out;
+    a.out_vals = c.vals_out;
+    a.dtype = p.dtype;
+    a.st = c.ly.status;
+    kern<<<(unsigned)p.P, kSegThreads, smem, c.stream>>>(a);
     return cudaGetLastError();
 }
 
