@@ -501,7 +501,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     const int64_t seg0 = imin64(len, warp * seg), seg1 = imin64(len, seg0 + seg);
     uint32_t *mine = wcnt + warp * NS;
     // keys of kAhead steps of 32 are loaded before the first is used
-    constexpr int kAhead = 4;
+    constexpr int kAhead = 8;
     uint32_t fa[kAhead];
     auto load_ahead = [&](int64_t e0) {
 #pragma unroll
@@ -606,6 +606,14 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
     const float inv_x = 1.0f / (float)xx;
     for (int64_t e0 = seg0; e0 < seg1; e0 += 32 * kAhead) {
         if (!stash) load_ahead(e0);
+        uint32_t va[kAhead];  // the payloads of the kAhead steps, loaded before the first is stored
+        if (runs_val) {
+#pragma unroll
+            for (int u = 0; u < kAhead; ++u) {
+                const int64_t e = e0 + u * 32 + lane;
+                va[u] = e < seg1 ? vals_in[lo + e] : 0u;
+            }
+        }
 #pragma unroll
         for (int u = 0; u < kAhead; ++u) {
             const int64_t e = e0 + u * 32 + lane;
@@ -625,7 +633,7 @@ run_sample_lowcard_kernel(const typename KeyTraits<DT>::T *__restrict__ keys, in
                 const uint32_t g1 = start[h] + mine[h] + (uint32_t)__popc(peers & lanemask_lt()) + 1;  // < 2^32
                 __syncwarp(act);
                 if (lane == __ffs(peers) - 1) mine[h] += (uint32_t)__popc(peers);
-                if (runs_val) runs_val[lo + g1 - 1] = vals_in[lo + e];  // payloads at their ranks
+                if (runs_val) runs_val[lo + g1 - 1] = va[u];  // payloads at their ranks
                 // j = g1 / x when x divides g1 (the quotient from a float
                 // estimate, corrected by one either way)
                 uint32_t j = (uint32_t)((float)g1 * inv_x);
