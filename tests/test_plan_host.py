@@ -73,3 +73,44 @@ def test_sub_bucket_limits():
         bsps.BSPS_ERR_TOO_LARGE
     rc, pl = _plan(bsps, 1 << 28, bsps.make_params(4096, sampling=bsps.BSPS_RANDOM))
     assert rc == 0 and pl.vbuckets == 4096 * pl.refine
+
+
+def _regular_inputs(n, p):
+    import numpy as np
+    import bsp_inputs as gen
+    yield "uniform", gen.uniform(n, p, 1)
+    yield "zero_entropy", gen.zero_entropy(n)
+    yield "staggered", gen.staggered(n, p, 2)
+    yield "bucket_sorted", gen.bucket_sorted(n, p, 3)
+    yield "det_duplicates", gen.det_duplicates(n, p, 4)
+    yield "2-G", gen.g_group(n, p, 5)
+    yield "zipf", gen.zipf(n, seed=6)
+    yield "ascending", np.arange(n, dtype=np.int32)
+    yield "descending", np.arange(n, dtype=np.int32)[::-1].copy()
+    rng = np.random.default_rng(7)
+    for t in range(20):  # few values: many keys tie with the splitters
+        yield f"values{t}", rng.integers(0, 2 + t % 5, n).astype(np.int32)
+
+
+@pytest.mark.parametrize("n,p,s,runs", [(4096, 8, 8, 8), (10_007, 16, 32, 16), (65_536, 64, 64, 128),
+                                        (30_000, 32, 16, 64), (5_000, 4, 200, 4)])
+def test_regular_capacity_holds_every_bucket_the_oracle_forms(n, p, s, runs):
+    """Regular oversampling sizes every bucket region by Lemma 5.1's bound, so
+    no input may give a bucket more records (keys and pads) than the plan's
+    capacity: checked against the buckets the oracle forms on the paper's
+    distributions, sorted and reversed input, and inputs of two to six values
+    whose keys tie with the splitters (the tie-break's worst case)."""
+    import numpy as np
+    import oracle
+    bsps = _lib()
+    rc, pl = _plan(bsps, n, bsps.make_params(p, s=s, runs=runs, sampling=bsps.BSPS_REGULAR, refine=1))
+    assert rc == 0 and pl.refine == 1
+    worst = 0
+    for name, keys in _regular_inputs(n, runs):
+        ref = oracle.sort(keys, p, s, runs, oracle.REGULAR, 0, want_sample=False)
+        assert int(ref.bucket_sizes.sum()) == n, name
+        worst = max(worst, int((ref.bucket_sizes + ref.pad_sizes).max()))
+    assert worst <= pl.capacity
+    # and the capacity is no looser than the lemma's bound (+1, rounded to 16 bytes)
+    x, q, R = pl.x, pl.q, pl.R
+    assert pl.capacity <= (((q + R - 1) * x - R + 2) + 3) // 4 * 4
