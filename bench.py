@@ -112,7 +112,7 @@ COMPARE = {"tree": ("tree", dict(classify=0)), "sort": ("bucket_sort_final_step"
            "tags": ("with_duplicate_handling", dict(duplicates=0))}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per key of each kernel from one
-# ncu capture (profiles/*.md), valid while the kernel source is unchanged:
+# ncu capture (its summary is under profiles/), valid while the kernel source is unchanged:
 # routing from the 2^26-key capture (4096 buckets, as at 2^28), the bucket sort
 # from the 2^27-key capture on [0, 2^30) (65,536-key buckets spanning 2^19
 # values on clusters of 8, as at 2^28);
